@@ -1,0 +1,161 @@
+"""Seeded synthetic two-plane light fields.
+
+Input generation only: this module holds none of the compression method's
+arithmetic.  Both the CPU oracle and the CUDA library are fed from here.
+
+A scene is a stack of fronto-parallel textured planes.  Plane k has disparity
+d_k pixels per unit of camera motion; a scene point X of plane k appears in
+view (i, j) at x = X + d_k (i - c_u), y = Y + d_k (j - c_v), with (c_u, c_v)
+the grid centre, so a renderer focused at disparity d_k (sampling view i at
+s + d (i - u)) brings that plane into focus.  Textures are multi-octave value
+noise (a random lattice per octave, bilinear, amplitude halved per octave);
+every plane but the farthest carries a value-noise opacity mask (> 0.5 is
+opaque) and nearer planes (larger disparity) cover farther ones.  Gaussian
+noise of standard deviation sigma is added per pixel and channel, then values
+are rounded and clipped to uint8.
+
+The presets follow the light fields of the paper's evaluation (grids of 5x5
+to 17x17 views of 64^2 to 1024^2 pixels) and are seeded with
+1805_06019 + preset id.  The real captures (Stanford archive) are not used.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 1805_06019
+
+PRESETS = {
+    # 5x5 views of 64x64, 3 planes, sigma 1; 2-level tree, tau 2.
+    "tiny": dict(id=0, U=5, V=5, W=64, H=64, disparities=[0.0, 0.5, 1.5], sigma=1.0,
+                 L=2, c=[0, 5], B=4, taus=[2], n_render=16, render_size=(64, 64)),
+    # 9x9 views of 512x512, 5 planes at -2..2, sigma 1; 3-level (3, 3), taus 1/4/8.
+    "plain": dict(id=1, U=9, V=9, W=512, H=512, disparities=[-2.0, -1.0, 0.0, 1.0, 2.0],
+                  sigma=1.0, L=3, c=[0, 3, 3], B=4, taus=[1, 4, 8], n_render=1000,
+                  render_size=(512, 512)),
+    # 17x17 views of 1024x1024, 8 planes at -3..3, contrast modulated; 3-level (5, 4).
+    "batching": dict(id=2, U=17, V=17, W=1024, H=1024,
+                     disparities=list(np.linspace(-3.0, 3.0, 8)), sigma=1.0,
+                     L=3, c=[0, 5, 4], B=4, taus=[4], n_requests=1_000_000,
+                     contrast=True),
+    # 15x15 views of 625x434, lenslet-like disparities within +-1, sigma 2; 3-level (3, 5).
+    "learned": dict(id=3, U=15, V=15, W=625, H=434, disparities=[-1.0, -0.4, 0.3, 1.0],
+                    sigma=2.0, L=3, c=[0, 3, 5], B=4, taus=[4]),
+    # serving light fields: 5x5x256^2, 9x9x512^2, 17x17x1024^2, 3-level each.
+    "serving_small": dict(id=4, U=5, V=5, W=256, H=256, disparities=[-1.0, 0.0, 1.0],
+                          sigma=1.0, L=3, c=[0, 2, 3], B=4, taus=[4]),
+    "serving_medium": dict(id=5, U=9, V=9, W=512, H=512, disparities=[-2.0, -1.0, 0.0, 1.0, 2.0],
+                           sigma=1.0, L=3, c=[0, 3, 3], B=4, taus=[4]),
+    "serving_large": dict(id=6, U=17, V=17, W=1024, H=1024,
+                          disparities=list(np.linspace(-3.0, 3.0, 8)), sigma=1.0,
+                          L=3, c=[0, 5, 4], B=4, taus=[4], contrast=True),
+}
+
+
+def rng_for(preset_id: int, stream: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([SEED_BASE + preset_id, stream]))
+
+
+def _shift_bilinear(img: np.ndarray, sx: float, sy: float) -> np.ndarray:
+    """out[y, x] = img sampled at (x - sx, y - sy), bilinear, wrapping."""
+    kx = int(np.floor(-sx))
+    fx = np.float32(-sx - kx)
+    ky = int(np.floor(-sy))
+    fy = np.float32(-sy - ky)
+    a = np.roll(img, -kx, axis=1)
+    if fx != 0:
+        a = (1 - fx) * a + fx * np.roll(a, -1, axis=1)
+    b = np.roll(a, -ky, axis=0)
+    if fy != 0:
+        b = (1 - fy) * b + fy * np.roll(b, -1, axis=0)
+    return b
+
+
+def value_noise(rng: np.random.Generator, H: int, W: int, cell: float,
+                octaves: int = 4, channels: int = 1) -> np.ndarray:
+    """[H, W, channels] float32 in [0, 1]: bilinear random lattices, octave o
+    at cell size cell / 2^o with amplitude 2^-o."""
+    out = np.zeros((H, W, channels), dtype=np.float32)
+    total = 0.0
+    for o in range(octaves):
+        cs = max(cell / (2 ** o), 1.0)
+        gh, gw = int(np.ceil(H / cs)) + 1, int(np.ceil(W / cs)) + 1
+        lat = rng.random((gh, gw, channels), dtype=np.float32)
+        ys = np.arange(H, dtype=np.float32) / cs
+        xs = np.arange(W, dtype=np.float32) / cs
+        y0 = np.floor(ys).astype(np.int64)
+        x0 = np.floor(xs).astype(np.int64)
+        fy = (ys - y0)[:, None, None]
+        fx = (xs - x0)[None, :, None]
+        y1 = np.minimum(y0 + 1, gh - 1)
+        x1 = np.minimum(x0 + 1, gw - 1)
+        top = lat[y0][:, x0] * (1 - fx) + lat[y0][:, x1] * fx
+        bot = lat[y1][:, x0] * (1 - fx) + lat[y1][:, x1] * fx
+        amp = 0.5 ** o
+        out += amp * (top * (1 - fy) + bot * fy)
+        total += amp
+    return out / np.float32(total)
+
+
+def make_lightfield(U: int, V: int, W: int, H: int, disparities, sigma: float,
+                    preset_id: int, contrast: bool = False) -> np.ndarray:
+    """Views [V*U, H, W, 3] uint8, view index j*U + i (i along u / x)."""
+    rng = rng_for(preset_id, 0)
+    cu, cv = (U - 1) / 2.0, (V - 1) / 2.0
+    order = np.argsort(np.asarray(disparities, dtype=np.float64), kind="stable")
+    planes = []
+    for rank, k in enumerate(order):
+        cell = float(rng.uniform(12.0, 40.0)) * max(W, H) / 512.0
+        lum = value_noise(rng, H, W, cell, 4, 1)
+        chroma = value_noise(rng, H, W, cell * 1.5, 3, 3)
+        tex = 0.75 * lum + 0.25 * chroma
+        if contrast:
+            # regional contrast: some areas nearly flat, some at full contrast,
+            # so that residual blocks range from very sparse to dense
+            m = value_noise(rng, H, W, max(W, H) / 6.0, 2, 1)
+            m = np.clip((m - 0.3) * 2.5, 0.0, 1.0) ** 2 * 0.95 + 0.05
+            tex = 0.5 + (tex - 0.5) * m * 1.6
+        tex = np.clip(tex, 0.0, 1.0) * np.float32(255.0)
+        mask = None
+        if rank > 0:
+            mask = value_noise(rng, H, W, cell * 2.0, 3, 1)
+        planes.append((float(disparities[k]), tex.astype(np.float32), mask))
+    noise_rng = rng_for(preset_id, 1)
+    out = np.empty((V * U, H, W, 3), dtype=np.uint8)
+    for j in range(V):
+        for i in range(U):
+            acc = None
+            for d, tex, mask in planes:
+                sx, sy = d * (i - cu), d * (j - cv)
+                layer = _shift_bilinear(tex, sx, sy)
+                if acc is None:
+                    acc = layer
+                else:
+                    opaque = _shift_bilinear(mask, sx, sy) > 0.5
+                    acc = np.where(opaque, layer, acc)
+            if sigma > 0:
+                acc = acc + noise_rng.normal(0.0, sigma, size=acc.shape).astype(np.float32)
+            out[j * U + i] = np.clip(np.rint(acc), 0, 255).astype(np.uint8)
+    return out
+
+
+def preset_lightfield(name: str) -> np.ndarray:
+    p = PRESETS[name]
+    return make_lightfield(p["U"], p["V"], p["W"], p["H"], p["disparities"], p["sigma"],
+                           p["id"], p.get("contrast", False))
+
+
+def random_views(n: int, U: int, V: int, preset_id: int, d_choices=(0.0,)) -> np.ndarray:
+    """[n, 3] float32 rows (u, v, d): camera positions uniform on the grid and a
+    focus disparity drawn from d_choices."""
+    rng = rng_for(preset_id, 2)
+    uv = rng.random((n, 2)) * np.array([U - 1, V - 1], dtype=np.float64)
+    d = rng.choice(np.asarray(d_choices, dtype=np.float64), size=n)
+    return np.concatenate([uv, d[:, None]], axis=1).astype(np.float32)
+
+
+def random_requests(n: int, n_views: int, n_loc: int, preset_id: int):
+    """n uniform random (view, location) block requests as two uint32 arrays."""
+    rng = rng_for(preset_id, 3)
+    views = rng.integers(0, n_views, size=n, dtype=np.uint32)
+    locs = rng.integers(0, n_loc, size=n, dtype=np.uint32)
+    return views, locs
