@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the RLFC hot path on GB300.
+
+One step = the whole hot path on one synthetic light field: decode every block
+of every view (Algorithm 2 over the full light field) and render n new views
+by quadrilinear interpolation with on-demand block decode (Section 3.6).
+Default workload: 9 x 9 views of 512 x 512 RGB, 5 textured planes at
+disparities -2..2, sigma 1 noise, 3-level tree (3, 3), 4 x 4 blocks,
+residual threshold 4 (the middle of the 1 / 4 / 8 sweep), 1000 new 512 x 512
+views at seeded random (u, v) with the focus on one of the planes.
+
+value = output pixels per second of the step (the 21.2 Mpx decoded light
+field plus 262 Mpx of rendered views) in Mpix/s; "parts" splits it into
+decode-all Mpix/s and rendered 512 x 512 views/s.  The stream is encoded once
+by the library's GPU encoder and stays resident; each timed step is bracketed
+by CUDA events on the launching stream after a 256 MiB write that flushes L2.
+
+--impl reference times the CPU oracle (the plain C restatement of the paper)
+on the host cores on a bounded sample of the same workload, scaled to the
+same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lf_synth  # noqa: E402
+
+METRIC = "decoded Mpix/s and % HBM roofline; 512×512 views/s; served p50/p99 view latency"
+UNIT = "Mpix/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(args):
+    p = dict(lf_synth.PRESETS[args.config])
+    n_views = args.n_views if args.n_views else p.get("n_render", 16)
+    W, H = p.get("render_size", (p["W"], p["H"]))
+    tau = args.tau if args.tau is not None else p["taus"][len(p["taus"]) // 2]
+    return p, n_views, W, H, tau
+
+
+def _config_json(p, n_views, out_w, out_h, tau, extra=None):
+    c = {"workload": f"{args_config_name(p)}: {p['U']}x{p['V']} views of {p['W']}x{p['H']} RGB, "
+                     f"{len(p['disparities'])} planes, sigma {p['sigma']}, {p['L']}-level tree {tuple(p['c'][1:])}, "
+                     f"4x4 blocks, tau {tau}; full decode + {n_views} new {out_w}x{out_h} views",
+         "U": p["U"], "V": p["V"], "W": p["W"], "H": p["H"], "levels": p["L"], "tau": tau,
+         "n_render": n_views, "render_size": [out_w, out_h],
+         "l2": "flushed by a 256 MiB write before every timed step"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def args_config_name(p):
+    for k, v in lf_synth.PRESETS.items():
+        if v["id"] == p["id"]:
+            return k
+    return "custom"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _algorithmic_bytes(info, n_views_lf, n_render, out_w, out_h):
+    nloc = info.nloc_x * info.nloc_y
+    stream_read = info.record_bytes + 4 * (3 * nloc + 1) + info.top_bytes
+    decode = stream_read + n_views_lf * info.W * info.H * 3
+    render = stream_read + n_render * out_w * out_h * 12
+    return decode, render, stream_read
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1805_06019_gb300 import rlfc
+
+    p, n_render, out_w, out_h, tau = _workload(args)
+    U, V = p["U"], p["V"]
+    lf = lf_synth.preset_lightfield(args_config_name(p))
+    d_lf = torch.from_numpy(lf).cuda()
+    data = rlfc.encode(d_lf, U, V, p["L"], p["c"], tau_p=tau, tau_b=16 * tau)
+    del d_lf
+    st = rlfc.Stream(data)
+    cams = lf_synth.random_views(n_render, U, V, p["id"], d_choices=p["disparities"])
+    uv = torch.from_numpy(cams[:, :2].copy()).cuda()
+    disp = torch.from_numpy(cams[:, 2].copy()).cuda()
+    out_lf = torch.empty((U * V, p["H"], p["W"], 3), dtype=torch.uint8, device="cuda")
+    out_views = torch.empty((n_render, out_h, out_w, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cur = torch.cuda.current_stream()
+
+    def step():
+        st.decode_all(out_lf)
+        st.render(uv, disp, out_w, out_h, out_views)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(str(torch.cuda.get_device_properties(local).uuid))
+    if not str(clocks.uuid).startswith("GPU-"):
+        clocks.uuid = "GPU-" + str(clocks.uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        a, b, c = evs[k]
+        a.record(cur)
+        st.decode_all(out_lf)
+        b.record(cur)
+        st.render(uv, disp, out_w, out_h, out_views)
+        c.record(cur)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_dec = [a.elapsed_time(b) for a, b, _ in evs]
+    t_ren = [b.elapsed_time(c) for _, b, c in evs]
+    step_ms = sum(t_dec) / args.steps + sum(t_ren) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms, sum(t_dec) / args.steps, sum(t_ren) / args.steps], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, dec_ms, ren_ms = t.tolist()
+    else:
+        dec_ms, ren_ms = sum(t_dec) / args.steps, sum(t_ren) / args.steps
+
+    info = st.info
+    px_lf = U * V * p["W"] * p["H"]
+    px_render = n_render * out_w * out_h
+    value = world * (px_lf + px_render) / (step_ms * 1e-3) / 1e6
+    peak, peak_src = _peaks()
+    b_dec, b_ren, stream_read = _algorithmic_bytes(info, U * V, n_render, out_w, out_h)
+    dec_gbs = b_dec / (dec_ms * 1e-3) / 1e9
+    ren_gbs = b_ren / (ren_ms * 1e-3) / 1e9
+    parts = {
+        "decode_all": {"ms": dec_ms, "mpix_s": px_lf / (dec_ms * 1e-3) / 1e6, "algorithmic_bytes": b_dec,
+                       "gbs": dec_gbs, "hbm_frac": dec_gbs / peak},
+        "render": {"ms": ren_ms, "views_per_s": n_render / (ren_ms * 1e-3), "mpix_s": px_render / (ren_ms * 1e-3) / 1e6,
+                   "algorithmic_bytes": b_ren, "gbs": ren_gbs, "hbm_frac": ren_gbs / peak},
+    }
+    dom = "render" if ren_ms >= dec_ms else "decode_all"
+    roof = {"bound": "hbm", "kernel": "render_tiled_kernel" if dom == "render" else "decode_all_kernel",
+            "achieved": parts[dom]["gbs"], "peak": peak, "unit": "GB/s", "frac": parts[dom]["gbs"] / peak,
+            "peak_source": f"{peak_src} hbm_gbs", "traffic": None}
+
+    # end to end through the C ABI: per-step camera upload from pinned host
+    # memory, decode + render, and download of every output to pinned memory
+    e2e = None
+    if not args.no_e2e:
+        h_uv = torch.from_numpy(cams[:, :2].copy()).pin_memory()
+        h_disp = torch.from_numpy(cams[:, 2].copy()).pin_memory()
+        h_lf = torch.empty(out_lf.shape, dtype=torch.uint8).pin_memory()
+        h_views = torch.empty(out_views.shape, dtype=torch.float32).pin_memory()
+        e_steps = min(args.steps, 5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(e_steps):
+            uv.copy_(h_uv, non_blocking=True)
+            disp.copy_(h_disp, non_blocking=True)
+            st.decode_all(out_lf)
+            st.render(uv, disp, out_w, out_h, out_views)
+            h_lf.copy_(out_lf, non_blocking=True)
+            h_views.copy_(out_views, non_blocking=True)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / e_steps
+        if world > 1:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * (px_lf + px_render) / (e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(h_uv.numel() * 4 + h_disp.numel() * 4),
+               "d2h_bytes_per_step": int(h_lf.numel() + h_views.numel() * 4), "steps": e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, lf, tau, n_render, out_w, out_h, cams, sample_views=args.cpu_sample_views)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": _config_json(p, n_render, out_w, out_h, tau,
+                                       {"stream_bytes": int(info.stream_bytes), "parallelism": f"replicas{world}"}),
+                "parts": parts, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 2 * args.steps, "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_stream(p, lf, tau):
+    import oracle
+    return oracle.Stream(oracle.encode(lf, p["U"], p["V"], B=4, L=p["L"], c=p["c"], tau_p=tau, tau_b=16 * tau))
+
+
+def _oracle_sample(p, st, n_render, out_w, out_h, cams, sample_views):
+    """Oracle time for decode-all plus `sample_views` renders, scaled to the
+    workload's n_render renders."""
+    import oracle
+    t0 = time.perf_counter()
+    dec = st.decode_all(nthreads=1)
+    t_dec = time.perf_counter() - t0
+    k = min(sample_views, n_render)
+    t0 = time.perf_counter()
+    for r in range(k):
+        oracle.render_view(dec, p["U"], p["V"], float(cams[r, 0]), float(cams[r, 1]), float(cams[r, 2]), out_w, out_h)
+    t_ren = time.perf_counter() - t0
+    step_s = t_dec + t_ren * n_render / k
+    px = p["U"] * p["V"] * p["W"] * p["H"] + n_render * out_w * out_h
+    return px / step_s / 1e6, step_s, t_dec + t_ren, k
+
+
+def cpu_baseline(p, lf, tau, n_render, out_w, out_h, cams, sample_views=50):
+    value, step_s, spent, k = _oracle_sample(p, _oracle_stream(p, lf, tau), n_render, out_w, out_h, cams,
+                                             sample_views)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle decode of all {p['U'] * p['V']} views plus {k} of the {n_render} renders "
+                      f"({spent:.1f} s, 1 thread), render time scaled to {n_render} views",
+            "step_s": step_s, "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    p, n_render, out_w, out_h, tau = _workload(args)
+    lf = lf_synth.preset_lightfield(args_config_name(p))
+    cams = lf_synth.random_views(n_render, p["U"], p["V"], p["id"], d_choices=p["disparities"])
+    k_views = 10
+    ost = _oracle_stream(p, lf, tau)
+    for _ in range(args.warmup):
+        _oracle_sample(p, ost, n_render, out_w, out_h, cams, k_views)
+    steps = [_oracle_sample(p, ost, n_render, out_w, out_h, cams, k_views) for _ in range(args.steps)]
+    step_s = float(np.mean([s[1] for s in steps]))
+    px = p["U"] * p["V"] * p["W"] * p["H"] + n_render * out_w * out_h
+    value = px / step_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": _config_json(p, n_render, out_w, out_h, tau),
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": f"per step: oracle decode of all {p['U'] * p['V']} views plus {k_views} "
+                                       f"renders (1 thread), render time scaled to {n_render} views"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="plain", choices=["plain", "tiny"])
+    ap.add_argument("--tau", type=int, default=None)
+    ap.add_argument("--n-views", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-views", type=int, default=50)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

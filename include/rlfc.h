@@ -1,0 +1,213 @@
+/*
+ * rlfc.h -- C ABI of the GB300 RLFC library (librlfc.so).
+ *
+ * RLFC (Pratapa & Manocha, I3D 2019) stores a light field as a tree: a few
+ * top-level representative key views (RKVs) plus sparse residual views (SRVs)
+ * cut into blocks and packed with bounded integer sequence encoding (BISE).
+ * Any block of any view can be decoded on its own ("random access", Section
+ * 3.5).  This library decodes such streams on one GPU and renders new views
+ * from them.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers owned by the caller; the library
+ *    never frees them.  Host pointers are only read during the call.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Compute calls only enqueue work on it and return
+ *    without synchronising; their outputs are valid once the stream reaches
+ *    that point.
+ *  - Every call returns RLFC_OK (0) or one of the RLFC_E_* codes.  Arguments
+ *    the host can check are checked before anything is enqueued; on error
+ *    nothing is written.  rlfc_strerror() turns a code into text and
+ *    rlfc_last_error() gives the detail of the most recent failure on the
+ *    calling thread.
+ *  - A loaded rlfc_stream is immutable: calls on different CUDA streams may
+ *    run concurrently against the same rlfc_stream.
+ *  - Device code never traps: a request the host cannot check (out-of-range
+ *    view or location inside a device array) gets a non-zero status byte and
+ *    a zeroed output block.
+ *
+ * Stream format v1 (all fields little-endian):
+ *   bytes 0..63   "RLFC", version 1, U, V, W, H, B, L, q, n_top, S, off_top,
+ *                 off_offsets, off_records, record_words, 0 (uint32 each)
+ *   then          per level l = 0..L-1 its node grid (Gu_l, Gv_l); then for
+ *                 every node of levels 0..L-2 (row-major per level) the index of
+ *                 its parent one level up
+ *   off_top       the n_top top-level RKVs, int16 YCoCg-R, [n_top][3][Hp][Wp]
+ *   off_offsets   3 * nloc + 1 uint32: start word of record (loc, channel) in
+ *                 the record section, then the total word count
+ *   off_records   the records, block locations row-major, channels Y, Co, Cg.
+ * The SRV nodes (all tree nodes below the top level) are numbered by a
+ * breadth-first search that starts from the top nodes in index order and
+ * visits children in increasing node index.  A record holds ceil(S/32) mask
+ * words (bit p set = SRV node p stores a block here), then one 18-bit header
+ * per stored block in BFS order (mode 0..27 in bits 0..4, extra shift in bits
+ * 5..6, block minimum as 11-bit two's complement in bits 7..17), then the
+ * blocks' BISE payloads in the same order, zero-padded to a 32-bit word.  Bit
+ * p of a record is bit p % 32 of its word p / 32.  Mode k codes values in
+ * [0, N_k) with N_k ascending over {1,2,3,4,5,6,8,10,12,16,...,768,1024}
+ * (2^b, 3*2^b, 5*2^b); a payload is the digit words first (trits: five per
+ * 8-bit base-3 word, quints: three per 7-bit base-5 word, a short last group
+ * taking ceil(8j/5) or ceil(7j/3) bits) and then each value's b low bits.  A
+ * stored value contributes (min + u) * 2^(q + shift) to its pixel.
+ */
+#ifndef RLFC_H
+#define RLFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RLFC_API __attribute__((visibility("default")))
+#else
+#define RLFC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum rlfc_status {
+    RLFC_OK = 0,
+    RLFC_E_INVALID_ARG = 1,  /* null pointer, zero size where not allowed, bad enum */
+    RLFC_E_FORMAT = 2,       /* stream bytes are corrupt or truncated */
+    RLFC_E_UNSUPPORTED = 3,  /* valid stream the kernels do not handle (e.g. B != 4) */
+    RLFC_E_CUDA = 4,         /* a CUDA runtime call failed */
+    RLFC_E_OOM = 5,          /* device or host allocation failed */
+    RLFC_E_RANGE = 6,        /* a size is beyond what the call supports */
+    RLFC_E_TIMEOUT = 7       /* a bounded device wait gave up */
+};
+
+/* Per-request status bytes written by rlfc_decode_blocks. */
+enum rlfc_request_status {
+    RLFC_REQ_OK = 0,
+    RLFC_REQ_BAD_VIEW = 1,
+    RLFC_REQ_BAD_LOCATION = 2
+};
+
+typedef struct rlfc_stream rlfc_stream;  /* opaque, library-owned */
+
+typedef struct {
+    uint32_t U, V;           /* camera grid: views are indexed j * U + i */
+    uint32_t W, H;           /* view size in pixels */
+    uint32_t B;              /* block side (pixels) */
+    uint32_t L;              /* tree levels, level 0 = the views */
+    uint32_t q;              /* global quantisation shift */
+    uint32_t n_top;          /* top-level RKVs */
+    uint32_t S;              /* SRV nodes (tree nodes below the top level) */
+    uint32_t Wp, Hp;         /* W, H rounded up to a multiple of B */
+    uint32_t nloc_x, nloc_y; /* block locations per row / column */
+    uint64_t stream_bytes;   /* size of the stream that was loaded */
+    uint64_t record_bytes;   /* SRV record section */
+    uint64_t top_bytes;      /* top RKV section */
+    uint64_t device_bytes;   /* device memory held by the loaded stream */
+} rlfc_info;
+
+/*
+ * Algorithm 2, initialisation (Section 3.5): parse and validate a stream held
+ * in host memory (nbytes bytes), rebuild the BFS numbering of the tree, and
+ * copy the top RKVs, the block offsets and the SRV records to the current
+ * CUDA device.  Every record is checked on the host (mask, modes, lengths)
+ * so that kernels never read past a record.  The copy is done on
+ * `cuda_stream` and the call returns after it completes, so host_bytes may be
+ * freed right away.  *out receives a handle to release with rlfc_free_stream.
+ * Errors: RLFC_E_INVALID_ARG, RLFC_E_FORMAT, RLFC_E_UNSUPPORTED, RLFC_E_OOM,
+ * RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_load_stream(const void *host_bytes, size_t nbytes, void *cuda_stream,
+                     rlfc_stream **out);
+
+/* Shape and sizes of a loaded stream. */
+RLFC_API int rlfc_stream_info(const rlfc_stream *s, rlfc_info *out);
+
+/* Release a loaded stream and its device memory (after its work finished). */
+RLFC_API void rlfc_free_stream(rlfc_stream *s);
+
+/*
+ * Algorithm 2 for every block of every view (the "decode all blocks"
+ * workload): d_out receives U*V*H*W*3 bytes, views in index order, each H rows
+ * of W RGB pixels (padding cropped).  Errors: RLFC_E_INVALID_ARG,
+ * RLFC_E_UNSUPPORTED, RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_decode_all(const rlfc_stream *s, uint8_t *d_out, void *cuda_stream);
+
+/*
+ * Algorithm 2, DecompressLFIBlock(ImgIdx, BlkIdx), for n independent random
+ * requests: request r decodes block location d_loc[r] (row-major, 0 <=
+ * loc < nloc_x * nloc_y) of view d_view[r] (0 <= view < U * V).  d_out
+ * receives n * B*B*3 bytes, request-major, each block B rows of B RGB pixels
+ * (padding included).  d_status (n bytes, may be NULL) receives an
+ * rlfc_request_status per request; a bad request gets a zeroed block.
+ * n = 0 is a no-op.  Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE (n >= 2^31),
+ * RLFC_E_UNSUPPORTED, RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
+                       size_t n, uint8_t *d_out, uint8_t *d_status, void *cuda_stream);
+
+/*
+ * Section 3.6: render n new views by quadrilinear interpolation of the
+ * decoded light field, decoding the needed blocks on demand from the
+ * compressed stream.  View r is seen from the continuous camera position
+ * (d_uv[2r], d_uv[2r+1]) on the U x V grid (clamped to [0,U-1] x [0,V-1]) with
+ * the focal plane at disparity d_disp[r] pixels per view.  Output pixel
+ * (x, y) of an out_w x out_h image follows the ray through
+ * s = (x + 0.5) W / out_w - 0.5, t = (y + 0.5) H / out_h - 0.5; in neighbour
+ * view (i, j) it samples (s + d (i - u), t + d (j - v)) bilinearly with
+ * clamp-to-edge, and the four views are blended bilinearly in (u, v).
+ * d_out receives n * out_h * out_w * 3 floats (RGB in [0, 1]), view-major.
+ * Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE, RLFC_E_UNSUPPORTED, RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_disp,
+                      uint32_t out_w, uint32_t out_h, size_t n, float *d_out,
+                      void *cuda_stream);
+
+/* Encoder parameters (Algorithm 1, Section 3.1-3.3). */
+typedef struct {
+    uint32_t U, V, W, H;  /* grid and view size */
+    uint32_t B;           /* block side; the GPU encoder supports 4 */
+    uint32_t L;           /* tree levels, 2..8 */
+    uint32_t c[8];        /* cluster side used to build level l from l-1 (c[1..L-1]) */
+    int32_t tau_p;        /* pixel threshold: |r| < tau_p is zeroed */
+    int32_t tau_b;        /* block energy threshold: sum |r| < tau_b drops the block */
+    uint32_t q;           /* global quantisation shift, 0..7 */
+} rlfc_enc_params;
+
+/*
+ * Algorithm 1 on the GPU: compress the views d_rgb (device, U*V*H*W*3 bytes,
+ * views in index order, RGB rows) into a format-v1 stream.  Every rule is
+ * integer arithmetic, so the output is byte-identical to any other encoder
+ * that follows them:
+ *  - views are padded to a multiple of B by repeating the last column / row
+ *    and converted to YCoCg-R (Section 4);
+ *  - level l's grid cuts level l-1's into k = ceil(G / c[l]) tiles per axis,
+ *    tile a covering [floor(a G / k), floor((a + 1) G / k)) (Eq. 1);
+ *  - a tile of mu x mv nodes is filtered with the binomial weights
+ *    C(mu-1, i) C(mv-1, j): RKV = floor((sum w X + 2^(s-1)) / 2^s),
+ *    s = mu + mv - 2 (Eq. 2);
+ *  - top-down, r = child RKV - parent reconstruction (Eq. 3); |r| < tau_p is
+ *    zeroed; a block whose sum |r| is below tau_b or zero is dropped; kept
+ *    values are quantised to sign(r) floor((|r| + 2^(q-1)) / 2^q) (no rounding
+ *    term when q = 0), a block quantising to all zeros is dropped, and the
+ *    child's reconstruction is parent + qv 2^q (Section 3.2);
+ *  - a stored block's header holds its minimum and the smallest mode whose
+ *    range holds max - min + 1 values (the cheapest one).
+ * On success *host_out holds *nbytes bytes allocated by the library
+ * (free with rlfc_free_host); the call synchronises `cuda_stream`.
+ * Errors: RLFC_E_INVALID_ARG, RLFC_E_UNSUPPORTED, RLFC_E_RANGE, RLFC_E_OOM,
+ * RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream,
+                void **host_out, size_t *nbytes);
+
+/* Free a host buffer returned by the library. */
+RLFC_API void rlfc_free_host(void *p);
+
+/* Static description of a status code. */
+RLFC_API const char *rlfc_strerror(int code);
+
+/* Detail of the most recent failure on the calling thread ("" if none). */
+RLFC_API const char *rlfc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLFC_H */

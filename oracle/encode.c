@@ -28,6 +28,19 @@
  *    qv - min are coded with the cheapest mode that holds their span.
  *  - Images whose side is not a multiple of B are padded by repeating the last
  *    column / row.
+ *
+ * Stream format v1 (little-endian):
+ *   bytes 0..63  "RLFC", version 1, U, V, W, H, B, L, q, n_top, S, off_top,
+ *                off_offsets, off_records, record_words, 0 (uint32 each);
+ *   then the node grid (Gu, Gv) of every level, then the parent index of every
+ *   node of levels 0..L-2;
+ *   off_top: top RKVs, int16 [n_top][channel][Hp][Wp];
+ *   off_offsets: 3 * nloc + 1 uint32, start word of record (loc, channel),
+ *   then the total;
+ *   off_records: per block location (row-major) and channel (Y, Co, Cg) a
+ *   record: ceil(S/32) presence words (bit p = SRV node at BFS position p has
+ *   a block), one 18-bit header per stored block (mode | shift << 5 |
+ *   (min & 0x7FF) << 7), then the BISE payloads, padded to 32 bits.
  */
 #include <stdlib.h>
 #include <string.h>

@@ -11,8 +11,7 @@
  *
  * Every function names the passage of the paper it follows.  Where the paper
  * is silent the oracle takes the reading written next to the function; the
- * stream layout is the one described in the repository's design notes
- * ("stream format v1").
+ * byte layout of the stream ("stream format v1") is stated in encode.c.
  *
  * Parity status: every function here is pinned by a CPU test against a closed
  * form, an exhaustive or brute-force check, a library routine or a stated

@@ -1,0 +1,64 @@
+// Internal state of a loaded RLFC stream and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rlfc.h"
+
+namespace rlfc {
+
+constexpr int kMaxLevels = 8;
+constexpr int kPadWords = 8;   // zero words after the records (bit-reader over-read)
+
+// Per BFS position: level (bits 0..3), parent reference (bits 4..17: the top
+// RKV index when the parent is the top level, else the parent's BFS
+// position), view index for level-0 nodes (bits 18..31).
+__host__ __device__ inline uint32_t node_level(uint32_t w) { return w & 15u; }
+__host__ __device__ inline uint32_t node_parent(uint32_t w) { return (w >> 4) & 0x3FFFu; }
+__host__ __device__ inline uint32_t node_view(uint32_t w) { return w >> 18; }
+
+struct Tables {
+    uint32_t L = 0, S = 0, n_top = 0, n_int = 0, n_views = 0;
+    std::vector<uint32_t> node_info;  // [S]
+    std::vector<uint32_t> view_anc;   // [n_views][kMaxLevels]: BFS position of the ancestor at
+                                      // levels 0..L-2, the top index at L-1
+};
+
+}  // namespace rlfc
+
+struct rlfc_stream {
+    rlfc_info info{};
+    int device = 0;
+    rlfc::Tables tab;
+    uint32_t MW = 0;            // mask words per record
+    uint64_t record_words = 0;
+    uint32_t max_record_words = 0;
+    uint32_t max_strip_words = 0;    // records of 32 consecutive locations of a row
+    // device buffers
+    uint32_t *d_records = nullptr;   // record_words + kPadWords
+    uint32_t *d_offsets = nullptr;   // 3 * nloc + 1
+    int16_t *d_top = nullptr;        // [n_top][nloc][3][16], block-major YCoCg-R
+    uint32_t *d_node_info = nullptr; // [S]
+    uint32_t *d_view_anc = nullptr;  // [n_views][kMaxLevels]
+};
+
+namespace rlfc {
+
+void set_error(const std::string &msg);
+int build_tables(uint32_t L, const std::vector<uint32_t> &cnt,
+                 const std::vector<std::vector<uint32_t>> &parent, Tables &t);
+int cuda_fail(cudaError_t e, const char *what);
+
+int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
+int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
+                         uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
+int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
+                  uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st);
+int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st,
+               std::vector<uint8_t> &out);
+
+}  // namespace rlfc

@@ -1,0 +1,193 @@
+"""Python binding of librlfc.so (include/rlfc.h).
+
+Argument marshalling only: torch tensors provide device memory and the CUDA
+stream; every step of decoding and rendering runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing or the device is
+not a CUDA GPU, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from .buildlib import LIB
+
+RLFC_OK = 0
+REQ_OK, REQ_BAD_VIEW, REQ_BAD_LOCATION = 0, 1, 2
+
+
+class RLFCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint32) for k in
+                ("U", "V", "W", "H", "B", "L", "q", "n_top", "S", "Wp", "Hp", "nloc_x", "nloc_y")] + \
+               [(k, ctypes.c_uint64) for k in ("stream_bytes", "record_bytes", "top_bytes", "device_bytes")]
+
+
+class EncParams(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_uint32), ("V", ctypes.c_uint32), ("W", ctypes.c_uint32),
+                ("H", ctypes.c_uint32), ("B", ctypes.c_uint32), ("L", ctypes.c_uint32),
+                ("c", ctypes.c_uint32 * 8), ("tau_p", ctypes.c_int32), ("tau_b", ctypes.c_int32),
+                ("q", ctypes.c_uint32)]
+
+
+EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
+           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_free_host",
+           "rlfc_strerror", "rlfc_last_error"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return LIB
+
+
+def lib():
+    """The loaded librlfc.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"librlfc.so not built ({LIB}); run paper_1805_06019_gb300.build()")
+            L = ctypes.CDLL(LIB)
+            vp, sz, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32
+            L.rlfc_load_stream.argtypes = [vp, sz, vp, ctypes.POINTER(vp)]
+            L.rlfc_stream_info.argtypes = [vp, ctypes.POINTER(Info)]
+            L.rlfc_free_stream.argtypes = [vp]
+            L.rlfc_free_stream.restype = None
+            L.rlfc_decode_all.argtypes = [vp, vp, vp]
+            L.rlfc_decode_blocks.argtypes = [vp, vp, vp, sz, vp, vp, vp]
+            L.rlfc_render_views.argtypes = [vp, vp, vp, u32, u32, sz, vp, vp]
+            L.rlfc_encode.argtypes = [ctypes.POINTER(EncParams), vp, vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
+            L.rlfc_free_host.argtypes = [vp]
+            L.rlfc_free_host.restype = None
+            L.rlfc_strerror.argtypes = [ctypes.c_int]
+            L.rlfc_strerror.restype = ctypes.c_char_p
+            L.rlfc_last_error.argtypes = []
+            L.rlfc_last_error.restype = ctypes.c_char_p
+            _lib = L
+        return _lib
+
+
+def _check(code: int):
+    if code != RLFC_OK:
+        L = lib()
+        raise RLFCError(code, f"{L.rlfc_strerror(code).decode()}: {L.rlfc_last_error().decode()}")
+
+
+def _stream_handle(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
+class Stream:
+    """A compressed light field resident on the current CUDA device
+    (rlfc_load_stream)."""
+
+    def __init__(self, data: bytes, stream=None):
+        L = lib()
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        h = ctypes.c_void_p()
+        _check(L.rlfc_load_stream(buf, len(data), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.info = Info()
+        _check(L.rlfc_stream_info(self._h, ctypes.byref(self.info)))
+        i = self.info
+        self.U, self.V, self.W, self.H, self.B, self.L = i.U, i.V, i.W, i.H, i.B, i.L
+        self.nloc_x, self.nloc_y = i.nloc_x, i.nloc_y
+        self.nloc = i.nloc_x * i.nloc_y
+        self.n_views = i.U * i.V
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rlfc_free_stream(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode_all(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Every view: [U*V, H, W, 3] uint8 (rlfc_decode_all)."""
+        if out is None:
+            out = torch.empty((self.n_views, self.H, self.W, 3), dtype=torch.uint8, device="cuda")
+        assert out.numel() == self.n_views * self.H * self.W * 3
+        _check(lib().rlfc_decode_all(self._h, ctypes.c_void_p(_dev(out, torch.uint8, "out")),
+                                     _stream_handle(stream)))
+        return out
+
+    def decode_blocks(self, views: torch.Tensor, locs: torch.Tensor, out: torch.Tensor | None = None,
+                      status: torch.Tensor | None = None, stream=None):
+        """Random blocks: (out [n, 4, 4, 3] uint8, status [n] uint8) (rlfc_decode_blocks)."""
+        n = views.numel()
+        if locs.numel() != n:
+            raise ValueError("views and locs differ in length")
+        if out is None:
+            out = torch.empty((n, self.B, self.B, 3), dtype=torch.uint8, device="cuda")
+        if status is None:
+            status = torch.empty((n,), dtype=torch.uint8, device="cuda")
+        if n == 0:
+            return out, status
+        _check(lib().rlfc_decode_blocks(
+            self._h, ctypes.c_void_p(_dev(views, torch.int32, "views") if views.dtype == torch.int32
+                                     else _dev(views, torch.uint32, "views")),
+            ctypes.c_void_p(_dev(locs, torch.int32, "locs") if locs.dtype == torch.int32
+                            else _dev(locs, torch.uint32, "locs")),
+            n, ctypes.c_void_p(_dev(out, torch.uint8, "out")),
+            ctypes.c_void_p(_dev(status, torch.uint8, "status")), _stream_handle(stream)))
+        return out, status
+
+    def render(self, uv: torch.Tensor, disp: torch.Tensor, out_w: int, out_h: int,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """New views: [n, out_h, out_w, 3] float32 in [0, 1] (rlfc_render_views)."""
+        n = disp.numel()
+        if uv.numel() != 2 * n:
+            raise ValueError("uv must hold two floats per view")
+        if out is None:
+            out = torch.empty((n, out_h, out_w, 3), dtype=torch.float32, device="cuda")
+        if n == 0:
+            return out
+        _check(lib().rlfc_render_views(
+            self._h, ctypes.c_void_p(_dev(uv, torch.float32, "uv")),
+            ctypes.c_void_p(_dev(disp, torch.float32, "disp")), out_w, out_h, n,
+            ctypes.c_void_p(_dev(out, torch.float32, "out")), _stream_handle(stream)))
+        return out
+
+
+def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: int = 0,
+           q: int = 0, B: int = 4, stream=None) -> bytes:
+    """Algorithm 1 on the GPU (rlfc_encode): views rgb [U*V, H, W, 3] uint8 on
+    the device -> stream bytes.  c[l] is the cluster side building level l."""
+    if rgb.dim() != 4 or rgb.shape[0] != U * V or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be [U*V, H, W, 3]")
+    p = EncParams()
+    p.U, p.V, p.W, p.H, p.B, p.L = U, V, rgb.shape[2], rgb.shape[1], B, L
+    for l in range(1, L):
+        p.c[l] = int(c[l])
+    p.tau_p, p.tau_b, p.q = int(tau_p), int(tau_b), int(q)
+    out = ctypes.c_void_p()
+    n = ctypes.c_size_t()
+    _check(lib().rlfc_encode(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")),
+                             _stream_handle(stream), ctypes.byref(out), ctypes.byref(n)))
+    try:
+        return ctypes.string_at(out, n.value)
+    finally:
+        lib().rlfc_free_host(out)

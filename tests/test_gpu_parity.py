@@ -1,0 +1,229 @@
+"""GPU parity through the C ABI against the CPU oracle.
+
+Decode (full and random access) and the GPU encoder must be bit-exact.
+Rendered views (fp32) must be within 1e-3 of the fp64 oracle on the [0, 1]
+scale, with at least 99.9 % of the 8-bit values identical after rounding.
+Inputs are the seeded synthetic light fields of lf_synth; every stream the
+GPU decodes here was written by the oracle's encoder.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lf_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RENDER_ATOL = 1e-3
+RENDER_U8_MIN_EQUAL = 0.999
+
+
+@pytest.fixture(scope="session")
+def rlfc():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1805_06019_gb300 import rlfc as mod
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return mod
+
+
+def _synthetic(U, V, W, H, seed, disparities=(0.0, 0.7, 1.6), sigma=1.0):
+    return lf_synth.make_lightfield(U, V, W, H, list(disparities), sigma, preset_id=100 + seed)
+
+
+# (name, U, V, W, H, L, c, tau_p, tau_b, q)
+CASES = [
+    ("tiny_preset", 5, 5, 64, 64, 2, [0, 5], 2, 32, 0),
+    ("lossless", 5, 5, 40, 24, 2, [0, 5], 0, 0, 0),
+    ("odd_sizes_3lvl", 6, 5, 30, 21, 3, [0, 2, 3], 3, 40, 0),
+    ("four_levels", 8, 8, 24, 24, 4, [0, 2, 2, 2], 2, 24, 0),
+    ("four_tops", 6, 6, 32, 32, 2, [0, 3], 1, 8, 0),
+    ("quantised", 5, 5, 20, 16, 3, [0, 2, 3], 0, 0, 2),
+    ("wide_strip", 3, 3, 260, 12, 2, [0, 3], 2, 16, 0),
+    ("all_dropped", 4, 4, 16, 16, 2, [0, 4], 10 ** 5, 10 ** 5, 0),
+]
+
+_cache = {}
+
+
+def _case(name):
+    if name not in _cache:
+        _, U, V, W, H, L, c, tp, tb, q = next(x for x in CASES if x[0] == name)
+        lf = lf_synth.preset_lightfield("tiny") if name == "tiny_preset" else _synthetic(U, V, W, H, len(_cache))
+        data = oracle.encode(lf, U, V, B=4, L=L, c=c, tau_p=tp, tau_b=tb, q=q)
+        _cache[name] = (lf, data, (U, V, W, H, L, c, tp, tb, q))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_encoder_matches_oracle(rlfc, name):
+    lf, data, (U, V, W, H, L, c, tp, tb, q) = _case(name)
+    got = rlfc.encode(torch.from_numpy(lf).cuda(), U, V, L, c, tau_p=tp, tau_b=tb, q=q)
+    assert len(got) == len(data)
+    assert got == data
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_decode_all_matches_oracle(rlfc, name):
+    lf, data, _ = _case(name)
+    ref = oracle.Stream(data).decode_all()
+    st = rlfc.Stream(data)
+    got = st.decode_all().cpu().numpy()
+    assert np.array_equal(got, ref)
+    if name == "lossless":
+        assert np.array_equal(got, lf)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_decode_blocks_matches_oracle(rlfc, name):
+    _, data, _ = _case(name)
+    ost = oracle.Stream(data)
+    st = rlfc.Stream(data)
+    n_views, nloc = st.n_views, st.nloc
+    if n_views * nloc <= 8000:
+        pairs = [(v, l) for v in range(n_views) for l in range(nloc)]
+    else:
+        rng = np.random.default_rng(3)
+        pairs = list(zip(rng.integers(0, n_views, 8000).tolist(), rng.integers(0, nloc, 8000).tolist()))
+    views = torch.tensor([p[0] for p in pairs], dtype=torch.int32, device="cuda")
+    locs = torch.tensor([p[1] for p in pairs], dtype=torch.int32, device="cuda")
+    out, status = st.decode_blocks(views, locs)
+    out = out.cpu().numpy()
+    assert int(status.max()) == 0
+    for r, (v, l) in enumerate(pairs):
+        assert np.array_equal(out[r], ost.decode_block(v, l)), (v, l)
+
+
+def test_decode_blocks_rejects_bad_requests_without_faulting(rlfc):
+    _, data, _ = _case("odd_sizes_3lvl")
+    ost = oracle.Stream(data)
+    st = rlfc.Stream(data)
+    pairs = [(0, 0), (st.n_views, 0), (3, st.nloc), (2 ** 31, 5), (st.n_views - 1, st.nloc - 1), (7, 2 ** 32 - 1)]
+    views = torch.tensor([p[0] for p in pairs], dtype=torch.int64).to(torch.uint32).cuda()
+    locs = torch.tensor([p[1] for p in pairs], dtype=torch.int64).to(torch.uint32).cuda()
+    out = torch.full((len(pairs), 4, 4, 3), 77, dtype=torch.uint8, device="cuda")
+    status = torch.full((len(pairs),), 9, dtype=torch.uint8, device="cuda")
+    st.decode_blocks(views, locs, out, status)
+    assert status.cpu().tolist() == [0, 1, 2, 1, 0, 2]
+    o = out.cpu().numpy()
+    assert np.array_equal(o[0], ost.decode_block(0, 0))
+    assert np.array_equal(o[4], ost.decode_block(st.n_views - 1, st.nloc - 1))
+    for r in (1, 2, 3, 5):
+        assert not o[r].any()
+
+
+def test_decode_blocks_unaligned_output_and_empty_batch(rlfc):
+    _, data, _ = _case("four_levels")
+    ost = oracle.Stream(data)
+    st = rlfc.Stream(data)
+    n = 37
+    rng = np.random.default_rng(4)
+    pv, pl = rng.integers(0, st.n_views, n), rng.integers(0, st.nloc, n)
+    buf = torch.zeros(n * 48 + 1, dtype=torch.uint8, device="cuda")
+    out = buf[1:].view(n, 4, 4, 3)
+    st.decode_blocks(torch.tensor(pv, dtype=torch.int32, device="cuda"),
+                     torch.tensor(pl, dtype=torch.int32, device="cuda"), out)
+    o = out.cpu().numpy()
+    for r in range(n):
+        assert np.array_equal(o[r], ost.decode_block(int(pv[r]), int(pl[r])))
+    e_out, e_status = st.decode_blocks(torch.zeros(0, dtype=torch.int32, device="cuda"),
+                                       torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert e_out.numel() == 0 and e_status.numel() == 0
+
+
+def _check_render(got: np.ndarray, want: np.ndarray):
+    err = np.abs(got.astype(np.float64) - want)
+    assert err.max() <= RENDER_ATOL, err.max()
+    eq = (oracle.to_u8(got.astype(np.float64)) == oracle.to_u8(want)).mean()
+    assert eq >= RENDER_U8_MIN_EQUAL, eq
+
+
+@pytest.mark.parametrize("name", ["tiny_preset", "odd_sizes_3lvl", "four_tops", "wide_strip"])
+@pytest.mark.parametrize("size", ["native", "up", "down"])
+def test_render_matches_oracle(rlfc, name, size):
+    _, data, (U, V, W, H, *_rest) = _case(name)
+    lf = oracle.Stream(data).decode_all()
+    out_w, out_h = {"native": (W, H), "up": (W * 3 // 2 + 1, H * 2 - 3), "down": (max(W // 3, 1), max(H // 2, 1))}[size]
+    rng = np.random.default_rng(5)
+    n = 12
+    uv = np.stack([rng.uniform(-0.3, U - 0.7, n), rng.uniform(-0.3, V - 0.7, n)], axis=1).astype(np.float32)
+    uv[0] = [0.0, 0.0]
+    uv[1] = [U - 1, V - 1]
+    uv[2] = [1.0, min(2.0, V - 1)]
+    disp = rng.choice([0.0, 0.7, -1.3, 2.5], n).astype(np.float32)
+    st = rlfc.Stream(data)
+    got = st.render(torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda(), out_w, out_h).cpu().numpy()
+    for r in range(n):
+        want = oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), out_w, out_h)
+        _check_render(got[r], want)
+
+
+def test_render_direct_path_for_heavy_downscale(rlfc):
+    # a 6 x 5 rendering of 300 x 280 views: the tiled kernel's footprint would
+    # not fit in shared memory, so the per-pixel path runs
+    U, V, W, H = 3, 3, 300, 280
+    lf0 = _synthetic(U, V, W, H, 40)
+    data = oracle.encode(lf0, U, V, B=4, L=2, c=[0, 3], tau_p=2, tau_b=32)
+    lf = oracle.Stream(data).decode_all()
+    uv = np.array([[0.5, 1.5], [2.0, 0.0], [1.2, 1.9]], dtype=np.float32)
+    disp = np.array([0.0, 3.0, -1.0], dtype=np.float32)
+    st = rlfc.Stream(data)
+    got = st.render(torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda(), 6, 5).cpu().numpy()
+    for r in range(3):
+        _check_render(got[r], oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), 6, 5))
+
+
+def test_single_row_grid_render(rlfc):
+    U, V, W, H = 4, 1, 24, 20
+    lf0 = _synthetic(U, V, W, H, 41)
+    data = oracle.encode(lf0, U, V, B=4, L=2, c=[0, 4], tau_p=1, tau_b=8)
+    lf = oracle.Stream(data).decode_all()
+    uv = np.array([[1.5, 0.0], [3.0, 0.4], [0.2, -1.0]], dtype=np.float32)
+    disp = np.array([0.5, 0.0, 1.0], dtype=np.float32)
+    st = rlfc.Stream(data)
+    got = st.render(torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda(), W, H).cpu().numpy()
+    for r in range(3):
+        _check_render(got[r], oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), W, H))
+
+
+# ---- the benchmark's workload at full size --------------------------------------
+
+@pytest.fixture(scope="module")
+def plain():
+    p = lf_synth.PRESETS["plain"]
+    lf = lf_synth.preset_lightfield("plain")
+    streams = {tau: oracle.encode(lf, p["U"], p["V"], B=4, L=p["L"], c=p["c"], tau_p=tau, tau_b=16 * tau)
+               for tau in p["taus"]}
+    return p, lf, streams
+
+
+def test_plain_full_decode_and_encode(rlfc, plain):
+    p, lf, streams = plain
+    d_lf = torch.from_numpy(lf).cuda()
+    for tau, data in streams.items():
+        assert rlfc.encode(d_lf, p["U"], p["V"], p["L"], p["c"], tau_p=tau, tau_b=16 * tau) == data
+        ref = oracle.Stream(data).decode_all(nthreads=8)
+        got = rlfc.Stream(data).decode_all().cpu().numpy()
+        assert np.array_equal(got, ref), tau
+
+
+def test_plain_render_1000_views_sampled(rlfc, plain):
+    p, _, streams = plain
+    data = streams[4]
+    lf = oracle.Stream(data).decode_all(nthreads=8)
+    cams = lf_synth.random_views(p["n_render"], p["U"], p["V"], p["id"], d_choices=p["disparities"])
+    st = rlfc.Stream(data)
+    W, H = p["render_size"]
+    out = st.render(torch.from_numpy(cams[:, :2].copy()).cuda(), torch.from_numpy(cams[:, 2].copy()).cuda(), W, H)
+    rng = np.random.default_rng(6)
+    n_s = 20000
+    vs, xs, ys = rng.integers(0, len(cams), n_s), rng.integers(0, W, n_s), rng.integers(0, H, n_s)
+    got = out[torch.from_numpy(vs).cuda(), torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()].cpu().numpy()
+    want = np.stack([oracle.render_pixel(lf, p["U"], p["V"], float(cams[v, 0]), float(cams[v, 1]),
+                                         float(cams[v, 2]), W, H, int(x), int(y))
+                     for v, x, y in zip(vs, xs, ys)])
+    _check_render(got, want)
+    # one whole view as well
+    want0 = oracle.render_view(lf, p["U"], p["V"], float(cams[0, 0]), float(cams[0, 1]), float(cams[0, 2]), W, H)
+    _check_render(out[0].cpu().numpy(), want0)
