@@ -132,11 +132,25 @@ def test_decode_blocks_unaligned_output_and_empty_batch(rlfc):
     assert e_out.numel() == 0 and e_status.numel() == 0
 
 
-def _check_render(got: np.ndarray, want: np.ndarray):
+TIE = 1e-4   # distance from k + 0.5 on the 8-bit scale below which both roundings are right
+
+
+def _check_render(got: np.ndarray, want: np.ndarray, min_equal: float | None = None):
+    """fp32 within RENDER_ATOL of fp64; 8-bit values identical except at exact
+    rounding ties (the fp64 value within TIE of k + 0.5), where either
+    neighbour is a correct rounding; optionally at least `min_equal` of all
+    8-bit values identical."""
     err = np.abs(got.astype(np.float64) - want)
     assert err.max() <= RENDER_ATOL, err.max()
-    eq = (oracle.to_u8(got.astype(np.float64)) == oracle.to_u8(want)).mean()
-    assert eq >= RENDER_U8_MIN_EQUAL, eq
+    a = oracle.to_u8(got.astype(np.float64)).astype(np.int32)
+    b = oracle.to_u8(want).astype(np.int32)
+    scaled = np.clip(want, 0.0, 1.0) * 255.0
+    tie = np.abs(scaled - np.floor(scaled) - 0.5) < TIE
+    ok = (a == b) | (tie & (np.abs(a - b) <= 1))
+    assert ok.all(), (int((~ok).sum()), float(err.max()))
+    if min_equal is not None:
+        eq = (a == b).mean()
+        assert eq >= min_equal, eq
 
 
 @pytest.mark.parametrize("name", ["tiny_preset", "odd_sizes_3lvl", "four_tops", "wide_strip"])
@@ -223,7 +237,7 @@ def test_plain_render_1000_views_sampled(rlfc, plain):
     want = np.stack([oracle.render_pixel(lf, p["U"], p["V"], float(cams[v, 0]), float(cams[v, 1]),
                                          float(cams[v, 2]), W, H, int(x), int(y))
                      for v, x, y in zip(vs, xs, ys)])
-    _check_render(got, want)
+    _check_render(got, want, RENDER_U8_MIN_EQUAL)
     # one whole view as well
     want0 = oracle.render_view(lf, p["U"], p["V"], float(cams[0, 0]), float(cams[0, 1]), float(cams[0, 2]), W, H)
-    _check_render(out[0].cpu().numpy(), want0)
+    _check_render(out[0].cpu().numpy(), want0, RENDER_U8_MIN_EQUAL)
