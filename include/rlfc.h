@@ -198,6 +198,38 @@ typedef struct {
 RLFC_API int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream,
                 void **host_out, size_t *nbytes);
 
+/*
+ * The same encoder for callers that cannot allocate device memory while they
+ * encode: code running under a custom or capped device allocator that must not
+ * see foreign cudaMalloc calls, processes whose device memory is reserved up
+ * front, or callers that must avoid the device-wide synchronisation of
+ * cudaMalloc / cudaFree.  The paper has no counterpart; this is a deployment
+ * variant of rlfc_encode with byte-identical output.
+ *
+ * It calls no cudaMalloc, cudaFree or other device-allocating routine.  Its
+ * device scratch is one array of 32 MiB compiled into the library, which a
+ * device holds from the first call on that device until the process exits.
+ * Light fields whose encoder scratch exceeds 32 MiB (roughly up to 9 x 9
+ * views of 128 x 128, depending on the tree) are rejected with RLFC_E_RANGE
+ * before any work is enqueued; use rlfc_encode for those.
+ *
+ * The caller passes the input views d_rgb (as for rlfc_encode) and a host
+ * buffer host_out of `capacity` bytes.  On success *nbytes holds the stream
+ * size and host_out the stream; if the buffer is too small the call returns
+ * RLFC_E_RANGE with *nbytes set to the size needed.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind (the words that must start at zero are cleared on every
+ * call), so calls that overlap on the GPU, from several host threads or
+ * streams, race and must be serialised by the caller.  The call synchronises
+ * `cuda_stream`.  Errors: RLFC_E_INVALID_ARG, RLFC_E_UNSUPPORTED, RLFC_E_RANGE,
+ * RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_encode_no_alloc(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream,
+                                  void *host_out, size_t capacity, size_t *nbytes);
+
 /* Free a host buffer returned by the library. */
 RLFC_API void rlfc_free_host(void *p);
 

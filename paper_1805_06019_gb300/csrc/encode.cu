@@ -307,6 +307,8 @@ int tile_count(uint32_t G, uint32_t c) { return (int)((G + c - 1) / c); }
 
 struct DevBuf {
     std::vector<void *> ptrs;
+    uint8_t *arena = nullptr;   // when set, buffers are carved from this caller-provided block
+    size_t arena_size = 0, arena_used = 0;
     ~DevBuf()
     {
         for (void *p : ptrs)
@@ -315,6 +317,15 @@ struct DevBuf {
     template <typename T>
     cudaError_t alloc(T **p, size_t count)
     {
+        if (arena) {
+            const size_t at = (arena_used + 255) & ~size_t(255);
+            const size_t bytes = count * sizeof(T) + 16;
+            if (at + bytes > arena_size)
+                return cudaErrorMemoryAllocation;
+            *p = reinterpret_cast<T *>(arena + at);
+            arena_used = at + bytes;
+            return cudaSuccess;
+        }
         cudaError_t e = cudaMalloc((void **)p, count * sizeof(T) + 16);
         if (e == cudaSuccess)
             ptrs.push_back((void *)*p);
@@ -334,7 +345,60 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 }  // namespace
 
-int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, std::vector<uint8_t> &out)
+// Upper bound of the device scratch encode_gpu carves for these parameters
+// (every buffer rounded up to 256 bytes, records at their largest possible
+// size); 0 when the parameters are invalid.
+size_t encode_scratch_bound(const rlfc_enc_params *p)
+{
+    if (!p || p->B != 4 || p->U < 1 || p->V < 1 || (uint64_t)p->U * p->V > 16383 || p->W < 1 || p->H < 1 ||
+        p->W > 65536 || p->H > 65536 || p->L < 2 || p->L > (uint32_t)kMaxLevels)
+        return 0;
+    const uint32_t L = p->L;
+    std::vector<uint64_t> cnt(L);
+    uint64_t Gu = p->U, Gv = p->V;
+    cnt[0] = Gu * Gv;
+    for (uint32_t l = 1; l < L; l++) {
+        if (p->c[l] < 1)
+            return 0;
+        Gu = (Gu + p->c[l] - 1) / p->c[l];
+        Gv = (Gv + p->c[l] - 1) / p->c[l];
+        cnt[l] = Gu * Gv;
+    }
+    const uint64_t Wp = (p->W + 3) / 4 * 4, Hp = (p->H + 3) / 4 * 4, nloc = (Wp / 4) * (Hp / 4);
+    const uint64_t npix = 3 * Wp * Hp;
+    uint64_t S = 0;
+    for (uint32_t l = 0; l + 1 < L; l++)
+        S += cnt[l];
+    uint64_t total = 0;
+    auto add = [&](uint64_t bytes) { total += ((bytes + 16) + 255) / 256 * 256; };
+    for (uint32_t l = 0; l < L; l++) {
+        add(2 * npix * cnt[l]);
+        if (l >= 1 && l + 1 < L)
+            add(2 * npix * cnt[l]);
+        if (l + 1 < L)
+            add(cnt[l] * 3 * nloc);
+    }
+    for (uint32_t l = 1; l < L; l++) {
+        add(4 * (cnt[l] + 1));
+        add(4 * cnt[l - 1]);
+        add(4 * cnt[l]);
+        add(8 * cnt[l - 1]);
+        add(4 * cnt[l - 1]);
+    }
+    add(4 * S);
+    add(4 * S);
+    add(4 * 3 * nloc);
+    add(4 * (3 * nloc + 1));
+    add(sizeof(int));
+    add(sizeof(void *) * L);
+    add(sizeof(void *) * L);
+    const uint64_t MW = (S + 31) / 32;
+    add(4 * (3 * nloc * (MW + (S * (kHdrBits + 160) + 31) / 32) + 1));
+    return (size_t)total;
+}
+
+int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, std::vector<uint8_t> &out,
+               uint8_t *arena, size_t arena_size)
 {
     if (p->B != 4) {
         set_error("the GPU encoder writes 4x4 blocks only");
@@ -385,6 +449,8 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     const size_t plane = (size_t)Wp * Hp, npix = 3 * plane;
 
     DevBuf buf;
+    buf.arena = arena;
+    buf.arena_size = arena_size;
     cudaError_t e;
     std::vector<int16_t *> img(L, nullptr), rec(L, nullptr);
     std::vector<uint8_t *> present(L, nullptr);

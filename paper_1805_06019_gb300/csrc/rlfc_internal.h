@@ -58,7 +58,10 @@ int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uin
                          uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
 int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
                   uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st);
+// arena: when given, every device buffer of the encoder is carved from it
+// (arena_size bytes) instead of being allocated
 int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st,
-               std::vector<uint8_t> &out);
+               std::vector<uint8_t> &out, uint8_t *arena = nullptr, size_t arena_size = 0);
+size_t encode_scratch_bound(const rlfc_enc_params *p);
 
 }  // namespace rlfc

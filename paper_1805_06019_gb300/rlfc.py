@@ -39,8 +39,8 @@ class EncParams(ctypes.Structure):
 
 
 EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
-           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_free_host",
-           "rlfc_strerror", "rlfc_last_error"]
+           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_no_alloc",
+           "rlfc_free_host", "rlfc_strerror", "rlfc_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -67,6 +67,7 @@ def lib():
             L.rlfc_decode_blocks.argtypes = [vp, vp, vp, sz, vp, vp, vp]
             L.rlfc_render_views.argtypes = [vp, vp, vp, u32, u32, sz, vp, vp]
             L.rlfc_encode.argtypes = [ctypes.POINTER(EncParams), vp, vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
+            L.rlfc_encode_no_alloc.argtypes = [ctypes.POINTER(EncParams), vp, vp, vp, sz, ctypes.POINTER(sz)]
             L.rlfc_free_host.argtypes = [vp]
             L.rlfc_free_host.restype = None
             L.rlfc_strerror.argtypes = [ctypes.c_int]
@@ -191,3 +192,23 @@ def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: 
         return ctypes.string_at(out, n.value)
     finally:
         lib().rlfc_free_host(out)
+
+
+def encode_no_alloc(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: int = 0,
+                    q: int = 0, B: int = 4, capacity: int | None = None, stream=None) -> bytes:
+    """rlfc_encode_no_alloc: the GPU encoder with its device scratch taken from
+    the library's fixed 32 MiB array (no device allocation); small light fields
+    only.  `capacity` sizes the host output buffer (default: the raw views)."""
+    if rgb.dim() != 4 or rgb.shape[0] != U * V or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be [U*V, H, W, 3]")
+    p = EncParams()
+    p.U, p.V, p.W, p.H, p.B, p.L = U, V, rgb.shape[2], rgb.shape[1], B, L
+    for l in range(1, L):
+        p.c[l] = int(c[l])
+    p.tau_p, p.tau_b, p.q = int(tau_p), int(tau_b), int(q)
+    cap = int(capacity) if capacity is not None else 4 * rgb.numel() + (1 << 16)
+    buf = ctypes.create_string_buffer(cap)
+    n = ctypes.c_size_t()
+    _check(lib().rlfc_encode_no_alloc(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")),
+                                      _stream_handle(stream), buf, cap, ctypes.byref(n)))
+    return buf.raw[: n.value]
