@@ -226,7 +226,8 @@ def run_ours(args):
                    "algorithmic_bytes": b_ren, "gbs": ren_gbs, "hbm_frac": ren_gbs / peak},
     }
     dom = "render" if ren_ms >= dec_ms else "decode_all"
-    roof = {"bound": "hbm", "kernel": "render_tiled_kernel" if dom == "render" else "decode_all_kernel",
+    render_kernel = "render_native_kernel" if (out_w, out_h) == (p["W"], p["H"]) else "render_tiled_kernel"
+    roof = {"bound": "hbm", "kernel": render_kernel if dom == "render" else "decode_all_kernel",
             "achieved": parts[dom]["gbs"], "peak": peak, "unit": "GB/s", "frac": parts[dom]["gbs"] / peak,
             "peak_source": f"{peak_src} hbm_gbs", "traffic": None}
 

@@ -75,8 +75,11 @@ __device__ __forceinline__ Camera make_camera(const Args &a, uint32_t n)
         const int ia = k & 1, jb = k >> 1;
         cam.view[k] = jv[jb] * (int)a.U + iv[ia];
         cam.w[k] = wu[ia] * wv[jb];
-        cam.shift_x[k] = d * ((float)iv[ia] - u);
-        cam.shift_y[k] = d * ((float)jv[jb] - v);
+        // a shift beyond twice the image size samples only the clamped edge
+        // either way; bounding it keeps the integer pixel arithmetic in range
+        const float lim = 2.0f * (float)max(a.W, a.H) + 4.0f;
+        cam.shift_x[k] = fminf(fmaxf(d * ((float)iv[ia] - u), -lim), lim);
+        cam.shift_y[k] = fminf(fmaxf(d * ((float)jv[jb] - v), -lim), lim);
     }
     return cam;
 }
@@ -264,6 +267,11 @@ __global__ void __launch_bounds__(256) render_direct_kernel(const Args a)
 int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
                   uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st)
 {
+    if (out_w == s->info.W && out_h == s->info.H) {
+        const int rc = launch_render_native(s, d_uv, d_disp, n, d_out, st);
+        if (rc != RLFC_E_UNSUPPORTED)
+            return rc;
+    }
     Args a;
     a.sv.records = s->d_records;
     a.sv.offsets = s->d_offsets;

@@ -56,6 +56,8 @@ int cuda_fail(cudaError_t e, const char *what);
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
                          uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
+int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t n,
+                         float *d_out, cudaStream_t st);
 int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
                   uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st);
 // arena: when given, every device buffer of the encoder is carved from it

@@ -201,6 +201,26 @@ def test_single_row_grid_render(rlfc):
         _check_render(got[r], oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), W, H))
 
 
+def test_native_render_many_views_per_cell_and_large_disparities(rlfc):
+    # 1500 views in two grid cells: more than one collection pass per CTA, and
+    # disparities up to 9 px/view so that views split into several groups
+    U, V, W, H = 3, 3, 72, 40
+    lf0 = _synthetic(U, V, W, H, 42)
+    data = oracle.encode(lf0, U, V, B=4, L=2, c=[0, 3], tau_p=2, tau_b=32)
+    lf = oracle.Stream(data).decode_all()
+    rng = np.random.default_rng(8)
+    n = 1500
+    cell = rng.integers(0, 2, n)
+    uv = np.stack([rng.uniform(0, 1, n) + cell, rng.uniform(0, 1, n) + (1 - cell)], axis=1).astype(np.float32)
+    disp = rng.uniform(-9.0, 9.0, n).astype(np.float32)
+    disp[:5] = [0.0, 1e9, -1e9, 400.0, -75.5]
+    st = rlfc.Stream(data)
+    got = st.render(torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda(), W, H).cpu().numpy()
+    for r in list(range(0, n, 7)) + list(range(5)):
+        want = oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), W, H)
+        _check_render(got[r], want)
+
+
 # ---- the benchmark's workload at full size --------------------------------------
 
 @pytest.fixture(scope="module")
