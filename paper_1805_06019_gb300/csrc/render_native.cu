@@ -17,14 +17,15 @@
 //     shifts fixes a padded window of the tile, and its clamp to the image a
 //     source rectangle;
 //  2. one thread per (block location, channel) walks the location's record
-//     once, in BFS order, decoding only the four neighbours' leaf blocks and
-//     their ancestors, and accumulates top RKV + residuals (YCoCg-R, int16)
-//     into the source rectangles;
-//  3. the windows are filled with packed RGB from the source rectangles,
-//     which replicates the image edge exactly as clamp-to-edge sampling does;
-//  4. per view, each thread blends 4 horizontally adjacent pixels from 2 x 5
-//     window samples per neighbour and writes them with three 16-byte
-//     streaming stores.
+//     once, in BFS order, and tables the payload offset and header of every
+//     node the four neighbours need (their leaves and ancestors);
+//  3. one thread per (block location, neighbour) adds the top RKV block and
+//     the neighbour's ancestors' residuals for the three channels, converts
+//     to RGB and writes the window cells whose clamped position is that pixel
+//     (which replicates the image edge as clamp-to-edge sampling does);
+//  4. per view, each thread blends one column of 4 pixels, sliding a 2 x 2
+//     stencil down the window (lanes read consecutive words, no bank
+//     conflicts), and writes with streaming stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,10 +36,13 @@ namespace rlfc {
 namespace {
 
 constexpr int kTW = 64, kTH = 16;       // output tile
-constexpr int kThreads = 256;           // 4 pixels per thread
+constexpr int kThreads = 256;           // one column of kRows pixels per thread
+constexpr int kRows = kTH * kTW / kThreads;
 constexpr int kListCap = 1024;          // views collected per pass
+constexpr int kGroupCap = 64;           // views whose parameters are cached per group
 constexpr int kMaxNeed = 4 * kMaxLevels;
 constexpr uint32_t kSmemBytes = 64 * 1024;
+constexpr uint32_t kDecodeFirstViews = 32;   // batches this large decode their views first
 
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
 
@@ -47,9 +51,10 @@ struct Args {
     const float *uv;
     const float *disp;
     float *out;
+    const uint32_t *decoded;   // packed RGB views [view][H][W] decoded for this call, or null
     uint32_t U, V, W, H, n;
     uint32_t tiles_x, cells_u;
-    uint32_t out_aligned16;
+    uint32_t need_max;   // distinct nodes four views can need: 4 (L - 1)
 };
 
 struct Shift {
@@ -108,27 +113,63 @@ __device__ __forceinline__ uint32_t cell_of(const Args &a, uint32_t r)
 }
 
 struct Window {
-    int wx0, wy0, WX, WY;     // padded window (global pixel origin, size)
-    int FW;                   // row stride of the window: WX + 3, so that a
-                              // 5-sample read of a ragged last group stays in the row
-    int sx0, sy0, SW, SH;     // source rectangle: the window clamped to the image
+    int wx0, wy0, WX, WY;     // padded window: global pixel origin and size
+    int FW;                   // row stride of the window (WX + 1)
+    int cx0, cy0, cx1, cy1;   // the window clamped to the image
     int oxmin, oymin;
-    uint32_t f_off, s_off;    // offsets (in 32-bit words) into shared memory
+    uint32_t f_off;           // offset (in 32-bit words) into shared memory
+};
+
+// Per view of the current group: the four neighbours' stencil weights (blend
+// weight / 255 times the bilinear weights; all zero for an unused neighbour)
+// and integer shifts.
+struct ViewP {
+    float w[4][4];            // [k][00, 10, 01, 11]
+    int16_t ox[4], oy[4];
 };
 
 extern __shared__ __align__(16) uint32_t g_dyn[];
 
-__global__ void __launch_bounds__(kThreads) render_native_kernel(const Args a)
+// Shared-memory words of the four neighbours' windows for a tile of tw x th
+// pixels with the given shift spreads, plus the per-location node table.
+__host__ __device__ __forceinline__ uint32_t window_words(int tw, int th, int sx, int sy)
+{
+    return (uint32_t)(tw + 2 + sx) * (uint32_t)(th + 1 + sy);
+}
+
+// One out-of-line copy of the block decoder keeps the kernel's code small
+// enough for the instruction cache.
+__device__ __noinline__ void decode_block_values(const uint32_t *rec, uint32_t pos, uint32_t mode, int32_t mn,
+                                                 int32_t scale, int32_t acc[kVals])
+{
+    int32_t u[kVals];
+    bise_decode16(rec, pos, mode, u);
+#pragma unroll
+    for (int v = 0; v < kVals; v++)
+        acc[v] += (mn + u[v]) * scale;
+}
+
+// Exact float of byte c of a packed RGB word: 2^23 + byte, built with one
+// byte permute, minus 2^23.
+__device__ __forceinline__ float byte_to_float(uint32_t p, int c)
+{
+    return __int_as_float((int)__byte_perm(p, 0x4Bu, (uint32_t)c | 0x4650u)) - 8388608.0f;
+}
+
+__global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a)
 {
     __shared__ uint32_t s_mode[kNumModes];
-    __shared__ uint32_t s_list[kListCap];
-    __shared__ int s_count, s_gstart, s_gend;
+    __shared__ uint16_t s_list[kListCap];
+    __shared__ ViewP s_vp[kGroupCap];
+    __shared__ int s_count, s_gend;
     __shared__ int s_oxmin[4], s_oxmax[4], s_oymin[4], s_oymax[4], s_used[4];
     __shared__ Window s_win[4];
-    __shared__ uint32_t s_need_pos[kMaxNeed], s_need_slots[kMaxNeed];
+    __shared__ uint32_t s_need_pos[kMaxNeed];
+    __shared__ int s_slot_need[4][kMaxLevels];
     __shared__ int s_nneed;
     __shared__ uint32_t s_top[4];
-    __shared__ int s_rect[4];   // union block rectangle bx0, by0, nbx, nby
+    __shared__ int s_rect[4];          // union block rectangle bx0, by0, nbx, nby
+    __shared__ uint32_t s_ent_off;     // word offset of the node table
 
     const int tid = threadIdx.x;
     const uint32_t cell = blockIdx.y;
@@ -137,7 +178,6 @@ __global__ void __launch_bounds__(kThreads) render_native_kernel(const Args a)
     const int tw = min(kTW, (int)a.W - tx0), th = min(kTH, (int)a.H - ty0);
     if (tid < kNumModes)
         s_mode[tid] = c_modes[tid];
-    // the four neighbour views of this cell
     int nview[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -153,70 +193,102 @@ __global__ void __launch_bounds__(kThreads) render_native_kernel(const Args a)
         const uint32_t lim = min(a.n, base + kListCap);
         for (uint32_t r = base + tid; r < lim; r += kThreads)
             if (cell_of(a, r) == cell)
-                s_list[atomicAdd(&s_count, 1)] = r;
+                s_list[atomicAdd(&s_count, 1)] = (uint16_t)r;
         __syncthreads();
         const int count = s_count;
-        if (count == 0)
-            continue;
-        // groups of views whose windows fit shared memory
         for (int g0 = 0; g0 < count;) {
-            if (tid == 0) {
-                // grow the group while the four windows fit
-                int oxl[4], oxh[4], oyl[4], oyh[4];
-                for (int k = 0; k < 4; k++) {
-                    oxl[k] = oyl[k] = INT_MAX;
-                    oxh[k] = oyh[k] = INT_MIN;
-                }
-                int g1 = g0;
-                while (g1 < count) {
-                    int c1, c2;
-                    float w[4];
-                    Shift sh[4];
-                    view_params(a, s_list[g1], c1, c2, w, sh);
-                    uint32_t words = 0;
-                    int nl[4], nh[4], ml[4], mh[4];
-                    for (int k = 0; k < 4; k++) {
-                        nl[k] = min(oxl[k], sh[k].ox);
-                        nh[k] = max(oxh[k], sh[k].ox);
-                        ml[k] = min(oyl[k], sh[k].oy);
-                        mh[k] = max(oyh[k], sh[k].oy);
-                        const uint32_t wx = (uint32_t)(tw + 1 + nh[k] - nl[k]), wy = (uint32_t)(th + 1 + mh[k] - ml[k]);
-                        words += (wx + 3) * wy + (3 * wx * wy + 1) / 2 + 8;
-                    }
-                    if (words * 4 > kSmemBytes && g1 > g0)
-                        break;
-                    for (int k = 0; k < 4; k++) {
-                        oxl[k] = nl[k];
-                        oxh[k] = nh[k];
-                        oyl[k] = ml[k];
-                        oyh[k] = mh[k];
-                    }
-                    g1++;
-                }
-                s_gstart = g0;
-                s_gend = g1;
-                for (int k = 0; k < 4; k++) {
-                    s_oxmin[k] = oxl[k];
-                    s_oxmax[k] = oxh[k];
-                    s_oymin[k] = oyl[k];
-                    s_oymax[k] = oyh[k];
-                    s_used[k] = 0;
-                }
+            // ---- per-view parameters of the next group, in parallel
+            const int gcap = min(kGroupCap, count - g0);
+            if (tid < 4) {
+                s_oxmin[tid] = s_oymin[tid] = INT_MAX;
+                s_oxmax[tid] = s_oymax[tid] = INT_MIN;
+                s_used[tid] = 0;
             }
             __syncthreads();
-            const int gs = s_gstart, ge = s_gend;
-            // neighbours with a non-zero weight for some view of the group
-            for (int q = gs + tid; q < ge; q += kThreads) {
+            if (tid < gcap) {
                 int c1, c2;
                 float w[4];
                 Shift sh[4];
-                view_params(a, s_list[q], c1, c2, w, sh);
-                for (int k = 0; k < 4; k++)
+                view_params(a, s_list[g0 + tid], c1, c2, w, sh);
+                ViewP &vp = s_vp[tid];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float wk = w[k] * (1.0f / 255.0f);
+                    vp.w[k][0] = wk * (1.0f - sh[k].fx) * (1.0f - sh[k].fy);
+                    vp.w[k][1] = wk * sh[k].fx * (1.0f - sh[k].fy);
+                    vp.w[k][2] = wk * (1.0f - sh[k].fx) * sh[k].fy;
+                    vp.w[k][3] = wk * sh[k].fx * sh[k].fy;
+                    vp.ox[k] = (int16_t)sh[k].ox;
+                    vp.oy[k] = (int16_t)sh[k].oy;
+                    atomicMin(&s_oxmin[k], sh[k].ox);
+                    atomicMax(&s_oxmax[k], sh[k].ox);
+                    atomicMin(&s_oymin[k], sh[k].oy);
+                    atomicMax(&s_oymax[k], sh[k].oy);
                     if (w[k] != 0.0f)
-                        s_used[k] = 1;
+                        atomicOr(&s_used[k], 1);
+                }
             }
             __syncthreads();
             if (tid == 0) {
+                // exact shared-memory words of the windows plus the node table
+                auto fits = [&](const int *oxl, const int *oxh, const int *oyl, const int *oyh, const int *used) {
+                    uint32_t words = 0;
+                    int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
+                    for (int k = 0; k < 4; k++) {
+                        words += window_words(tw, th, oxh[k] - oxl[k], oyh[k] - oyl[k]);
+                        if (!used[k])
+                            continue;
+                        bx0 = min(bx0, min(max(tx0 + oxl[k], 0), (int)a.W - 1) / kBlock);
+                        bx1 = max(bx1, min(max(tx0 + tw + oxh[k], 0), (int)a.W - 1) / kBlock);
+                        by0 = min(by0, min(max(ty0 + oyl[k], 0), (int)a.H - 1) / kBlock);
+                        by1 = max(by1, min(max(ty0 + th + oyh[k], 0), (int)a.H - 1) / kBlock);
+                    }
+                    words = (words + 3) & ~3u;
+                    if (!a.decoded)
+                        words += (uint32_t)((bx1 - bx0 + 1) * (by1 - by0 + 1) * 3 * 2) * a.need_max;
+                    return words * 4 <= kSmemBytes;
+                };
+                int ge = g0 + gcap;
+                if (!fits(s_oxmin, s_oxmax, s_oymin, s_oymax, s_used)) {
+                    // rare (a large disparity spread): the longest prefix that fits
+                    int oxl[4], oxh[4], oyl[4], oyh[4], used[4];
+                    for (int k = 0; k < 4; k++) {
+                        oxl[k] = oyl[k] = INT_MAX;
+                        oxh[k] = oyh[k] = INT_MIN;
+                        used[k] = 0;
+                    }
+                    ge = g0;
+                    while (ge < g0 + gcap) {
+                        const ViewP &vp = s_vp[ge - g0];
+                        int nl[4], nh[4], ml[4], mh[4], nu[4];
+                        for (int k = 0; k < 4; k++) {
+                            nl[k] = min(oxl[k], (int)vp.ox[k]);
+                            nh[k] = max(oxh[k], (int)vp.ox[k]);
+                            ml[k] = min(oyl[k], (int)vp.oy[k]);
+                            mh[k] = max(oyh[k], (int)vp.oy[k]);
+                            nu[k] = used[k] | (vp.w[k][0] != 0.0f || vp.w[k][1] != 0.0f || vp.w[k][2] != 0.0f ||
+                                               vp.w[k][3] != 0.0f);
+                        }
+                        if (ge > g0 && !fits(nl, nh, ml, mh, nu))
+                            break;
+                        for (int k = 0; k < 4; k++) {
+                            oxl[k] = nl[k];
+                            oxh[k] = nh[k];
+                            oyl[k] = ml[k];
+                            oyh[k] = mh[k];
+                            used[k] = nu[k];
+                        }
+                        ge++;
+                    }
+                    for (int k = 0; k < 4; k++) {
+                        s_oxmin[k] = oxl[k];
+                        s_oxmax[k] = oxh[k];
+                        s_oymin[k] = oyl[k];
+                        s_oymax[k] = oyh[k];
+                        s_used[k] = used[k];
+                    }
+                }
+                s_gend = ge;
                 uint32_t off = 0;
                 int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
                 for (int k = 0; k < 4; k++) {
@@ -227,103 +299,99 @@ __global__ void __launch_bounds__(kThreads) render_native_kernel(const Args a)
                     wn.wy0 = ty0 + s_oymin[k];
                     wn.WX = tw + 1 + s_oxmax[k] - s_oxmin[k];
                     wn.WY = th + 1 + s_oymax[k] - s_oymin[k];
-                    wn.FW = wn.WX + 3;
-                    wn.sx0 = min(max(wn.wx0, 0), (int)a.W - 1);
-                    wn.sy0 = min(max(wn.wy0, 0), (int)a.H - 1);
-                    const int sx1 = min(max(wn.wx0 + wn.WX - 1, 0), (int)a.W - 1);
-                    const int sy1 = min(max(wn.wy0 + wn.WY - 1, 0), (int)a.H - 1);
-                    wn.SW = sx1 - wn.sx0 + 1;
-                    wn.SH = sy1 - wn.sy0 + 1;
+                    wn.FW = wn.WX + 1;
+                    wn.cx0 = min(max(wn.wx0, 0), (int)a.W - 1);
+                    wn.cx1 = min(max(wn.wx0 + wn.WX - 1, 0), (int)a.W - 1);
+                    wn.cy0 = min(max(wn.wy0, 0), (int)a.H - 1);
+                    wn.cy1 = min(max(wn.wy0 + wn.WY - 1, 0), (int)a.H - 1);
                     wn.f_off = off;
                     off += (uint32_t)(wn.FW * wn.WY);
-                    wn.s_off = off;
-                    off += (uint32_t)(3 * wn.SW * wn.SH + 1) / 2;
-                    off = (off + 3) & ~3u;
                     if (s_used[k]) {
-                        bx0 = min(bx0, wn.sx0 / kBlock);
-                        by0 = min(by0, wn.sy0 / kBlock);
-                        bx1 = max(bx1, sx1 / kBlock);
-                        by1 = max(by1, sy1 / kBlock);
+                        bx0 = min(bx0, wn.cx0 / kBlock);
+                        by0 = min(by0, wn.cy0 / kBlock);
+                        bx1 = max(bx1, wn.cx1 / kBlock);
+                        by1 = max(by1, wn.cy1 / kBlock);
                     }
                 }
                 s_rect[0] = bx0;
                 s_rect[1] = by0;
                 s_rect[2] = bx1 - bx0 + 1;
                 s_rect[3] = by1 - by0 + 1;
-                // BFS positions the four neighbours need, ascending, with the
-                // neighbours each one serves
+                s_ent_off = (off + 3) & ~3u;
+                // BFS positions the used neighbours need, ascending
                 int nn = 0;
                 for (int k = 0; k < 4; k++) {
-                    if (!s_used[k])
-                        continue;
                     const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
                     s_top[k] = anc[a.sv.L - 1];
+                    if (!s_used[k])
+                        continue;
                     for (uint32_t l = 0; l + 1 < a.sv.L; l++) {
                         const uint32_t p = anc[l];
                         int e = 0;
                         while (e < nn && s_need_pos[e] != p)
                             e++;
-                        if (e == nn) {
-                            s_need_pos[nn] = p;
-                            s_need_slots[nn] = 0;
-                            nn++;
-                        }
-                        s_need_slots[e] |= 1u << k;
+                        if (e == nn)
+                            s_need_pos[nn++] = p;
                     }
                 }
                 for (int x = 1; x < nn; x++)   // insertion sort by position
                     for (int y = x; y > 0 && s_need_pos[y - 1] > s_need_pos[y]; y--) {
-                        const uint32_t tp = s_need_pos[y], ts = s_need_slots[y];
+                        const uint32_t tp = s_need_pos[y];
                         s_need_pos[y] = s_need_pos[y - 1];
-                        s_need_slots[y] = s_need_slots[y - 1];
                         s_need_pos[y - 1] = tp;
-                        s_need_slots[y - 1] = ts;
                     }
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
+                    for (uint32_t l = 0; l + 1 < a.sv.L; l++) {
+                        int e = -1;
+                        if (s_used[k])
+                            for (e = 0; s_need_pos[e] != anc[l]; e++) {
+                            }
+                        s_slot_need[k][l] = e;
+                    }
+                }
                 s_nneed = nn;
             }
             __syncthreads();
+            const int ge = s_gend;
+            const int nbx = s_rect[2], nloc_r = nbx * s_rect[3];
+            const int nn = s_nneed;
+            // node table entry (2 words) of needed node e at union location li, channel c:
+            // [0] payload offset (bits 0..21) | mode << 22 | shift << 27 | present << 31
+            // [1] the block minimum (sign-extended)
+            uint32_t *ent = g_dyn + s_ent_off;
 
-            // ---- phase 2: one record walk per (block location, channel)
-            const int nbx = s_rect[2], ntask = nbx * s_rect[3] * 3;
-            for (int task = tid; task < ntask; task += kThreads) {
+            if (a.decoded) {
+                // ---- phase 2 (decoded views): copy the windows, clamped to the image
+                for (int k = 0; k < 4; k++) {
+                    if (!s_used[k])
+                        continue;
+                    const Window &wn = s_win[k];
+                    const uint32_t *img = a.decoded + (size_t)nview[k] * a.W * a.H;
+                    uint32_t *f = g_dyn + wn.f_off;
+                    for (int i = tid; i < wn.WX * wn.WY; i += kThreads) {
+                        const int r = i / wn.WX, cc = i - r * wn.WX;
+                        const int gx = min(max(wn.wx0 + cc, 0), (int)a.W - 1);
+                        const int gy = min(max(wn.wy0 + r, 0), (int)a.H - 1);
+                        f[r * wn.FW + cc] = __ldg(img + (size_t)gy * a.W + gx);
+                    }
+                }
+                __syncthreads();
+            } else {
+            // ---- phase 2a: one walk per (location, channel)
+            for (int task = tid; task < nloc_r * 3; task += kThreads) {
                 const int c = task % 3, li = task / 3;
                 const int bx = s_rect[0] + li % nbx, by = s_rect[1] + li / nbx;
                 const uint32_t loc = (uint32_t)by * a.sv.nlx + (uint32_t)bx;
-                // which neighbours' source rectangles this block overlaps
-                uint32_t touch = 0;
-                for (int k = 0; k < 4; k++) {
-                    const Window &wn = s_win[k];
-                    if (s_used[k] && bx * kBlock + kBlock - 1 >= wn.sx0 && bx * kBlock <= wn.sx0 + wn.SW - 1 &&
-                        by * kBlock + kBlock - 1 >= wn.sy0 && by * kBlock <= wn.sy0 + wn.SH - 1)
-                        touch |= 1u << k;
-                }
-                if (!touch)
-                    continue;
-                // top RKV values first
-                for (int k = 0; k < 4; k++) {
-                    if (!((touch >> k) & 1u))
-                        continue;
-                    const Window &wn = s_win[k];
-                    int16_t *src = reinterpret_cast<int16_t *>(g_dyn + wn.s_off) + c * wn.SW * wn.SH;
-                    const int16_t *tp = a.sv.top + ((size_t)s_top[k] * a.sv.nloc + loc) * 48 + c * 16;
-#pragma unroll
-                    for (int v = 0; v < kVals; v++) {
-                        const int px = bx * kBlock + (v & 3) - wn.sx0, py = by * kBlock + (v >> 2) - wn.sy0;
-                        if (px >= 0 && px < wn.SW && py >= 0 && py < wn.SH)
-                            src[py * wn.SW + px] = tp[v];
-                    }
-                }
                 const uint32_t *rec = a.sv.records + a.sv.offsets[3 * loc + c];
+                uint32_t *my = ent + (size_t)(li * 3 + c) * 2 * nn;
                 uint32_t P = 0;
                 for (uint32_t m = 0; m < a.sv.MW; m++)
                     P += __popc(rec[m]);
                 const uint32_t hdr0 = 32 * a.sv.MW;
                 uint32_t rank = 0, off = hdr0 + kHdrBits * P, cur = 0;
-                const int nn = s_nneed;
                 for (int e = 0; e < nn; e++) {
                     const uint32_t p = s_need_pos[e];
-                    const uint32_t use = s_need_slots[e] & touch;
-                    // stored blocks in [cur, p): skip their payloads
                     uint32_t rp = rank;
                     for (uint32_t m = cur >> 5; m <= (p >> 5); m++) {
                         uint32_t word = rec[m];
@@ -337,112 +405,152 @@ __global__ void __launch_bounds__(kThreads) render_native_kernel(const Args a)
                         off += mode_bits(s_mode[get_bits(rec, hdr0 + kHdrBits * h, 5)]);
                     rank = rp;
                     cur = p + 1;
-                    if (!((rec[p >> 5] >> (p & 31u)) & 1u))
-                        continue;
-                    const BlockHeader hd = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
-                    const uint32_t m = s_mode[hd.mode];
-                    if (use) {
-                        int32_t u[kVals];
-                        bise_decode16(rec, off, m, u);
-                        const int32_t scale = 1 << (a.sv.q + hd.shift);
-                        for (int k = 0; k < 4; k++) {
-                            if (!((use >> k) & 1u))
-                                continue;
-                            const Window &wn = s_win[k];
-                            int16_t *src = reinterpret_cast<int16_t *>(g_dyn + wn.s_off) + c * wn.SW * wn.SH;
-#pragma unroll
-                            for (int v = 0; v < kVals; v++) {
-                                const int px = bx * kBlock + (v & 3) - wn.sx0, py = by * kBlock + (v >> 2) - wn.sy0;
-                                if (px >= 0 && px < wn.SW && py >= 0 && py < wn.SH)
-                                    src[py * wn.SW + px] = (int16_t)(src[py * wn.SW + px] + (hd.min + u[v]) * scale);
-                            }
-                        }
+                    if ((rec[p >> 5] >> (p & 31u)) & 1u) {
+                        const BlockHeader hd = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
+                        my[2 * e] = off | (hd.mode << 22) | (hd.shift << 27) | 0x80000000u;
+                        my[2 * e + 1] = (uint32_t)hd.min;
+                        off += mode_bits(s_mode[hd.mode]);
+                        rank++;
+                    } else {
+                        my[2 * e] = 0u;
                     }
-                    off += mode_bits(m);
-                    rank++;
                 }
             }
             __syncthreads();
 
-            // ---- phase 3: padded windows of packed RGB (edge replicated)
-            for (int k = 0; k < 4; k++) {
+            // ---- phase 2b: per (location, neighbour): top RKV + ancestors'
+            // residuals for the three channels, RGB, into the window (pixels on
+            // the image edge also fill the window cells beyond it)
+            for (int task = tid; task < nloc_r * 4; task += kThreads) {
+                const int k = task & 3, li = task >> 2;
                 if (!s_used[k])
                     continue;
                 const Window &wn = s_win[k];
-                const int16_t *src = reinterpret_cast<const int16_t *>(g_dyn + wn.s_off);
-                const int plane = wn.SW * wn.SH;
+                const int bx = s_rect[0] + li % nbx, by = s_rect[1] + li / nbx;
+                if (bx * kBlock + kBlock - 1 < wn.cx0 || bx * kBlock > wn.cx1 ||
+                    by * kBlock + kBlock - 1 < wn.cy0 || by * kBlock > wn.cy1)
+                    continue;
+                const uint32_t loc = (uint32_t)by * a.sv.nlx + (uint32_t)bx;
+                uint32_t pk[3][kVals / 2];   // finished channels as int16 pairs
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    int32_t acc[kVals];
+                    const uint4 *tp = reinterpret_cast<const uint4 *>(
+                        a.sv.top + ((size_t)s_top[k] * a.sv.nloc + loc) * 48 + c * 16);
+                    const uint4 t0 = tp[0], t1 = tp[1];
+                    const uint32_t t32[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                    for (int v = 0; v < kVals; v++)
+                        acc[v] = (int32_t)(int16_t)(t32[v >> 1] >> (16 * (v & 1)));
+                    const uint32_t *rec = a.sv.records + a.sv.offsets[3 * loc + c];
+                    const uint32_t *my = ent + (size_t)(li * 3 + c) * 2 * nn;
+                    for (uint32_t l = 0; l + 1 < a.sv.L; l++) {
+                        const int e = s_slot_need[k][l];
+                        const uint32_t w0 = my[2 * e];
+                        if (!(w0 >> 31))
+                            continue;
+                        decode_block_values(rec, w0 & 0x3FFFFFu, s_mode[(w0 >> 22) & 31u], (int32_t)my[2 * e + 1],
+                                            1 << (a.sv.q + ((w0 >> 27) & 3u)), acc);
+                    }
+#pragma unroll
+                    for (int v = 0; v < kVals; v += 2)
+                        pk[c][v >> 1] = ((uint32_t)acc[v] & 0xFFFFu) | ((uint32_t)acc[v + 1] << 16);
+                }
                 uint32_t *f = g_dyn + wn.f_off;
-                for (int i = tid; i < wn.WX * wn.WY; i += kThreads) {
-                    const int r = i / wn.WX, cc = i - r * wn.WX;
-                    const int gx = min(max(wn.wx0 + cc, 0), (int)a.W - 1) - wn.sx0;
-                    const int gy = min(max(wn.wy0 + r, 0), (int)a.H - 1) - wn.sy0;
-                    const int at = gy * wn.SW + gx;
-                    f[r * wn.FW + cc] = ycocg_to_rgb24(src[at], src[plane + at], src[2 * plane + at]);
+#pragma unroll
+                for (int v = 0; v < kVals; v++) {
+                    const int px = bx * kBlock + (v & 3), py = by * kBlock + (v >> 2);
+                    if (px < wn.cx0 || px > wn.cx1 || py < wn.cy0 || py > wn.cy1)
+                        continue;
+                    const int sh16 = 16 * (v & 1);
+                    const uint32_t rgb = ycocg_to_rgb24((int16_t)(pk[0][v >> 1] >> sh16), (int16_t)(pk[1][v >> 1] >> sh16),
+                                                        (int16_t)(pk[2][v >> 1] >> sh16));
+                    // window columns whose clamped x is px (more than one on the image edge)
+                    const int xa = (px == 0 ? wn.wx0 : px) - wn.wx0, xb = (px == (int)a.W - 1 ? wn.wx0 + wn.WX - 1 : px) - wn.wx0;
+                    const int ya = (py == 0 ? wn.wy0 : py) - wn.wy0, yb = (py == (int)a.H - 1 ? wn.wy0 + wn.WY - 1 : py) - wn.wy0;
+                    for (int yy = max(ya, 0); yy <= min(yb, wn.WY - 1); yy++)
+                        for (int xx = max(xa, 0); xx <= min(xb, wn.WX - 1); xx++)
+                            f[yy * wn.FW + xx] = rgb;
                 }
             }
             __syncthreads();
 
-            // ---- phase 4: blend and store, view by view
-            const int row = tid / (kTW / 4), col = (tid % (kTW / 4)) * 4;
-            for (int q = gs; q < ge; q++) {
-                const uint32_t r = s_list[q];
-                int c1, c2;
-                float w[4];
-                Shift sh[4];
-                view_params(a, r, c1, c2, w, sh);
-                if (row >= th || col >= tw)
+            }
+            // ---- phase 4: blend and store, view by view; thread = one column
+            // of kRows rows, sliding the 2 x 2 stencil down the window
+            const int col = tid % kTW, r0 = (tid / kTW) * kRows;
+            const bool active = col < tw && r0 < th;
+            for (int q = g0; q < ge; q++) {
+                if (!active)
                     continue;
-                float acc[4][3];
+                const ViewP &vp = s_vp[q - g0];
+                float acc[kRows][3];
 #pragma unroll
-                for (int p = 0; p < 4; p++)
-                    acc[p][0] = acc[p][1] = acc[p][2] = 0.0f;
-#pragma unroll
+                for (int rr = 0; rr < kRows; rr++)
+                    acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
+#pragma unroll 1
                 for (int k = 0; k < 4; k++) {
-                    if (w[k] == 0.0f)
+                    const float w00 = vp.w[k][0], w10 = vp.w[k][1], w01 = vp.w[k][2], w11 = vp.w[k][3];
+                    if (w00 == 0.0f && w10 == 0.0f && w01 == 0.0f && w11 == 0.0f)
                         continue;
                     const Window &wn = s_win[k];
-                    const float wk = w[k] * (1.0f / 255.0f);
-                    const float w00 = wk * (1.0f - sh[k].fx) * (1.0f - sh[k].fy), w10 = wk * sh[k].fx * (1.0f - sh[k].fy);
-                    const float w01 = wk * (1.0f - sh[k].fx) * sh[k].fy, w11 = wk * sh[k].fx * sh[k].fy;
-                    const uint32_t *f0 = g_dyn + wn.f_off + (row + sh[k].oy - wn.oymin) * wn.FW + (col + sh[k].ox - wn.oxmin);
-                    const uint32_t *f1 = f0 + wn.FW;
-                    uint32_t A[5], Bv[5];
+                    const uint32_t *f = g_dyn + wn.f_off + (r0 + vp.oy[k] - wn.oymin) * wn.FW + (col + vp.ox[k] - wn.oxmin);
+                    float a0[3], a1[3];
+                    {
+                        const uint32_t p0 = f[0], p1 = f[1];
 #pragma unroll
-                    for (int x = 0; x < 5; x++) {
-                        A[x] = f0[x];
-                        Bv[x] = f1[x];
+                        for (int ch = 0; ch < 3; ch++) {
+                            a0[ch] = byte_to_float(p0, ch);
+                            a1[ch] = byte_to_float(p1, ch);
+                        }
                     }
 #pragma unroll
-                    for (int ch = 0; ch < 3; ch++) {
-                        float a5[5], b5[5];
+                    for (int rr = 0; rr < kRows; rr++) {
+                        if (r0 + rr >= th)
+                            break;   // the window holds rows up to th + spread only
+                        f += wn.FW;
+                        const uint32_t p0 = f[0], p1 = f[1];
 #pragma unroll
-                        for (int x = 0; x < 5; x++) {
-                            a5[x] = (float)((A[x] >> (8 * ch)) & 255u);
-                            b5[x] = (float)((Bv[x] >> (8 * ch)) & 255u);
+                        for (int ch = 0; ch < 3; ch++) {
+                            const float b0 = byte_to_float(p0, ch), b1 = byte_to_float(p1, ch);
+                            acc[rr][ch] += w00 * a0[ch] + w10 * a1[ch] + w01 * b0 + w11 * b1;
+                            a0[ch] = b0;
+                            a1[ch] = b1;
                         }
-#pragma unroll
-                        for (int p = 0; p < 4; p++)
-                            acc[p][ch] += w00 * a5[p] + w10 * a5[p + 1] + w01 * b5[p] + w11 * b5[p + 1];
                     }
                 }
-                const int y = ty0 + row, x = tx0 + col;
-                float *o = a.out + (((size_t)r * a.H + y) * a.W + x) * 3;
-                if (a.out_aligned16 && col + 4 <= tw) {
-                    float4 *o4 = reinterpret_cast<float4 *>(o);
-                    __stcs(o4 + 0, make_float4(acc[0][0], acc[0][1], acc[0][2], acc[1][0]));
-                    __stcs(o4 + 1, make_float4(acc[1][1], acc[1][2], acc[2][0], acc[2][1]));
-                    __stcs(o4 + 2, make_float4(acc[2][2], acc[3][0], acc[3][1], acc[3][2]));
-                } else {
-                    for (int p = 0; p < 4 && col + p < tw; p++) {
-                        o[3 * p] = acc[p][0];
-                        o[3 * p + 1] = acc[p][1];
-                        o[3 * p + 2] = acc[p][2];
-                    }
+                const uint32_t r = s_list[q];
+#pragma unroll
+                for (int rr = 0; rr < kRows; rr++) {
+                    if (r0 + rr >= th)
+                        break;
+                    float *o = a.out + (((size_t)r * a.H + (ty0 + r0 + rr)) * a.W + (tx0 + col)) * 3;
+                    // evict-first: the outputs stream through L2 without pushing out the stream
+                    __stcs(o, acc[rr][0]);
+                    __stcs(o + 1, acc[rr][1]);
+                    __stcs(o + 2, acc[rr][2]);
                 }
             }
             g0 = ge;
             __syncthreads();
         }
+    }
+}
+
+// Marks the neighbour views that each camera blends with a non-zero weight.
+__global__ void mark_needed_kernel(const Args a, uint8_t *needed)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n)
+        return;
+    int ci, cj;
+    float w[4];
+    Shift sh[4];
+    view_params(a, r, ci, cj, w, sh);
+    for (int k = 0; k < 4; k++) {
+        const int i = a.U == 1 ? 0 : ci + (k & 1), j = a.V == 1 ? 0 : cj + (k >> 1);
+        if (w[k] != 0.0f)
+            needed[j * (int)a.U + i] = 1;
     }
 }
 
@@ -476,9 +584,11 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     const uint32_t tiles_y = (a.H + kTH - 1) / kTH;
     a.cells_u = a.U > 1 ? a.U - 1 : 1;
     const uint32_t cells_v = a.V > 1 ? a.V - 1 : 1;
-    a.out_aligned16 = ((uintptr_t)d_out & 15u) == 0 && (a.W % 4) == 0;
-    // a single view needs windows of (64+1) x (16+1) pixels per neighbour
-    const uint32_t single = 4 * ((kTW + 4) * (kTH + 1) + (3 * (kTW + 1) * (kTH + 1) + 1) / 2 + 8) * 4;
+    // a single view (no shift spread) needs four windows of the full tile
+    // and the node table of its footprint
+    a.need_max = 4 * (a.sv.L - 1);
+    const uint32_t single = 4 * (4 * window_words(kTW, kTH, 0, 0) +
+                                 ((kTW + 7) / kBlock + 1) * ((kTH + 7) / kBlock + 1) * 3 * 2 * a.need_max);
     if (single > kSmemBytes || (uint64_t)a.tiles_x * tiles_y >= (1u << 31) || a.cells_u * cells_v > 65535)
         return RLFC_E_UNSUPPORTED;
     cudaError_t e = cudaFuncSetAttribute(render_native_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -486,6 +596,35 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     if (e != cudaSuccess)
         return cuda_fail(e, "render_native: shared memory attribute");
     dim3 grid(a.tiles_x * tiles_y, a.cells_u * cells_v);
+    // Batches of many views decode the views they need once into a transient
+    // packed-RGB buffer (stream-ordered allocation, freed on the same stream);
+    // small batches decode block by block inside the render kernel.
+    a.decoded = nullptr;
+    void *scratch = nullptr;
+    const size_t view_words = (size_t)a.W * a.H;
+    const size_t mask_bytes = (a.sv.n_views + 255) / 256 * 256;
+    if (n >= kDecodeFirstViews &&
+        cudaMallocAsync(&scratch, mask_bytes + 4 * view_words * a.sv.n_views, st) == cudaSuccess) {
+        uint8_t *needed = static_cast<uint8_t *>(scratch);
+        uint32_t *decoded = reinterpret_cast<uint32_t *>(needed + mask_bytes);
+        int rc = RLFC_OK;
+        if ((e = cudaMemsetAsync(needed, 0, mask_bytes, st)) != cudaSuccess)
+            rc = cuda_fail(e, "render: clearing the view mask");
+        if (rc == RLFC_OK) {
+            mark_needed_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, needed);
+            rc = launch_decode_packed(s, decoded, needed, st);
+        }
+        if (rc == RLFC_OK) {
+            a.decoded = decoded;
+            render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+            e = cudaGetLastError();
+            if (e != cudaSuccess)
+                rc = cuda_fail(e, "render_native launch");
+        }
+        cudaFreeAsync(scratch, st);
+        return rc;
+    }
+    cudaGetLastError();   // a failed stream-ordered allocation only selects the other path
     render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -54,6 +54,8 @@ int build_tables(uint32_t L, const std::vector<uint32_t> &cnt,
 int cuda_fail(cudaError_t e, const char *what);
 
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
+// every view the mask marks (all when null), as packed RGB words [view][H][W]
+int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, cudaStream_t st);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
                          uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
 int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t n,

@@ -221,6 +221,25 @@ def test_native_render_many_views_per_cell_and_large_disparities(rlfc):
         _check_render(got[r], want)
 
 
+def test_native_render_batch_equals_single_view_calls(rlfc):
+    # a batch of 48 views decodes its views first; one view per call decodes
+    # blocks inside the render kernel: both must give identical bits
+    _, data, (U, V, W, H, *_rest) = _case("odd_sizes_3lvl")
+    lf = oracle.Stream(data).decode_all()
+    rng = np.random.default_rng(9)
+    n = 48
+    uv = np.stack([rng.uniform(0, U - 1, n), rng.uniform(0, V - 1, n)], axis=1).astype(np.float32)
+    disp = rng.choice([0.0, 0.7, -1.3], n).astype(np.float32)
+    st = rlfc.Stream(data)
+    batch = st.render(torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda(), W, H).cpu().numpy()
+    for r in range(n):
+        one = st.render(torch.from_numpy(uv[r:r + 1].copy()).cuda(), torch.from_numpy(disp[r:r + 1].copy()).cuda(),
+                        W, H).cpu().numpy()[0]
+        assert np.array_equal(one, batch[r]), r
+    for r in range(0, n, 5):
+        _check_render(batch[r], oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]), W, H))
+
+
 # ---- the benchmark's workload at full size --------------------------------------
 
 @pytest.fixture(scope="module")
