@@ -1,33 +1,39 @@
 // Full light-field decode: Algorithm 2 for every (view, block location).
 //
-// One CTA owns a strip of kStrip consecutive block locations of one block row.
-// The strip's records are contiguous in the stream (location-major, then
-// Y / Co / Cg), so they are staged into shared memory with coalesced 16-byte
-// loads, together with the strip's top-RKV blocks.  Three walker warps (one per
-// channel, lane = location) then walk their record once in BFS order:
-// internal nodes (levels >= 1) are reconstructed into shared memory as
-// parent + residual, leaves (the views) are reconstructed the same way in
-// batches of kLeafBatch, converted from YCoCg-R to RGB by all four warps and
-// written as whole 384-byte image rows.  Every SRV block of the strip is thus
-// decoded exactly once and every output byte written once.
+// One CTA owns a strip of kStrip consecutive block locations of one block
+// row; their 3 * kStrip records (location-major, then Y / Co / Cg) and
+// top-RKV blocks are read once.  Phases:
+//  1. scan: one warp per record counts the stored blocks (popcounts of the
+//     presence mask) and turns the closed-form payload lengths of their
+//     headers into payload offsets with a warp scan;
+//  2. internal nodes (levels >= 1, first in BFS order): the stored blocks are
+//     compacted into a work list and decoded lane-per-value by half-warps
+//     (no lane idles on an absent node), then the levels are added top-down:
+//     reconstruction = parent reconstruction (or top RKV) + residual;
+//  3. the views (leaves), kLeafBatch at a time: compacted, decoded the same
+//     way into a residual buffer, then parent + residual is converted from
+//     YCoCg-R to RGB and written as whole image rows with 16-byte stores.
+// Every stored block of the strip is decoded once and every output byte is
+// written once.
 //
 // A second instantiation writes one packed RGB word per pixel (r | g << 8 |
-// b << 16, 512-byte rows) and decodes only the views a per-view mask asks for;
-// the renderer uses it to decode, from the compressed stream, just the views a
-// batch of new cameras samples.
+// b << 16) and decodes only the views a per-view mask asks for; the renderer
+// uses it to decode, from the compressed stream, just the views a batch of
+// new cameras samples.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
-#include "rlfc_device.cuh"
-#include "rlfc_internal.h"
+#include "warp_decode.cuh"
 
 namespace rlfc {
 namespace {
 
-constexpr int kStrip = 32;       // block locations per CTA
-constexpr int kThreads = 128;
+constexpr int kStrip = 16;       // block locations per CTA
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int kLeafBatch = 8;
+constexpr int kRecs = 3 * kStrip;
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
@@ -42,156 +48,229 @@ struct Args {
     uint32_t S, n_int, n_top, L, q, MW;
     uint32_t nlx, nloc, W, H;
     uint32_t out_aligned16; // output base is 16-byte aligned
-    uint32_t node_words;   // S rounded up to 4
-    uint32_t stage_words;  // capacity of the record staging area (multiple of 4)
+    uint32_t pmax;          // largest number of stored blocks in one record
+    uint32_t list_cap;      // work-list capacity (items)
 };
 
-// Decode SRV node p of a record into v (zeros when the node has no block).
-__device__ __forceinline__ void decode_node(const uint32_t *rec, uint32_t p, uint32_t &hdr_pos,
-                                            uint32_t &pay_pos, const uint32_t *s_mode, uint32_t q,
-                                            int32_t v[kVals])
-{
-    if ((rec[p >> 5] >> (p & 31u)) & 1u) {
-        const BlockHeader h = unpack_header(get_bits(rec, hdr_pos, kHdrBits));
-        hdr_pos += kHdrBits;
-        const uint32_t m = s_mode[h.mode];
-        int32_t u[kVals];
-        bise_decode16(rec, pay_pos, m, u);
-        pay_pos += mode_bits(m);
-        const int32_t scale = 1 << (q + h.shift);
-#pragma unroll
-        for (int k = 0; k < kVals; k++)
-            v[k] = (h.min + u[k]) * scale;
-    } else {
-#pragma unroll
-        for (int k = 0; k < kVals; k++)
-            v[k] = 0;
-    }
-}
-
-// Step past SRV node p of a record without decoding it.
-__device__ __forceinline__ void skip_node(const uint32_t *rec, uint32_t p, uint32_t &hdr_pos, uint32_t &pay_pos,
-                                          const uint32_t *s_mode)
-{
-    if ((rec[p >> 5] >> (p & 31u)) & 1u) {
-        pay_pos += mode_bits(s_mode[get_bits(rec, hdr_pos, 5)]);
-        hdr_pos += kHdrBits;
-    }
-}
+struct Smem {
+    uint32_t *node;    // [S]
+    int16_t *top;      // [n_top][48][kStrip]
+    int16_t *inter;    // [n_int][48][kStrip]  internal reconstructions
+    int16_t *res;      // [kLeafBatch][48][kStrip]  leaf residuals
+    uint8_t *rgb;      // [kLeafBatch * 4][row bytes]
+    uint32_t *mask;    // [kRecs][MW]
+    uint32_t *off;     // [kRecs][pmax]  payload bit offset of each stored block
+    uint2 *list;       // [list_cap]  (node | record << 16, rank)
+};
 
 extern __shared__ __align__(16) unsigned char g_smem[];
+
+__host__ __device__ inline size_t r16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__device__ __forceinline__ Smem carve(const Args &a)
+{
+    Smem m;
+    unsigned char *p = g_smem;
+    m.node = reinterpret_cast<uint32_t *>(p);
+    p += r16(4ull * a.S);
+    m.top = reinterpret_cast<int16_t *>(p);
+    p += r16(2ull * a.n_top * 48 * kStrip);
+    m.inter = reinterpret_cast<int16_t *>(p);
+    p += r16(2ull * a.n_int * 48 * kStrip);
+    m.res = reinterpret_cast<int16_t *>(p);
+    p += r16(2ull * kLeafBatch * 48 * kStrip);
+    m.rgb = p;
+    p += r16((size_t)kLeafBatch * 4 * kStrip * 16);
+    m.mask = reinterpret_cast<uint32_t *>(p);
+    p += r16(4ull * kRecs * a.MW);
+    m.off = reinterpret_cast<uint32_t *>(p);
+    p += r16(4ull * kRecs * a.pmax);
+    m.list = reinterpret_cast<uint2 *>(p);
+    return m;
+}
+
+inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap)
+{
+    return r16(4ull * S) + r16(2ull * n_top * 48 * kStrip) + r16(2ull * n_int * 48 * kStrip) +
+           r16(2ull * kLeafBatch * 48 * kStrip) + r16((size_t)kLeafBatch * 4 * kStrip * 16) +
+           r16(4ull * kRecs * MW) + r16(4ull * kRecs * pmax) + r16(8ull * list_cap);
+}
+
+// Stored blocks of nodes [p0, p1) over the strip's records, compacted into the
+// work list: (node | record << 16, rank).  Returns the item count.
+__device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uint32_t p0, uint32_t p1,
+                                               uint32_t *s_count, bool use_mask)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0)
+        *s_count = 0;
+    __syncthreads();
+    const uint32_t pairs = (p1 - p0) * kRecs;
+    for (uint32_t i0 = 0; i0 < pairs; i0 += kThreads) {
+        const uint32_t i = i0 + tid;
+        bool present = false;
+        uint32_t p = 0, r = 0, rank = 0;
+        if (i < pairs) {
+            p = p0 + i / kRecs;
+            r = i % kRecs;
+            const uint32_t *mk = m.mask + r * a.MW;
+            present = (mk[p >> 5] >> (p & 31u)) & 1u;
+            if (present && use_mask)
+                present = a.needed[node_view(m.node[p])] != 0;
+            if (present) {
+                for (uint32_t w = 0; w < (p >> 5); w++)
+                    rank += __popc(mk[w]);
+                rank += __popc(mk[p >> 5] & ((1u << (p & 31u)) - 1u));
+            }
+        }
+        const unsigned bal = __ballot_sync(kFullMask, present);
+        uint32_t base = 0;
+        if (lane == 0 && bal)
+            base = atomicAdd(s_count, (uint32_t)__popc(bal));
+        base = __shfl_sync(kFullMask, base, 0);
+        if (present)
+            m.list[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(p | (r << 16), rank);
+    }
+    __syncthreads();
+    return *s_count;
+}
+
+// Decode the listed blocks, a half-warp per block, lane = value; the
+// residual (min + u) * 2^(q + shift) goes to the node's slot in dst:
+// dst[((node - p0) * 48 + channel * 16 + value) * kStrip + location].
+__device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
+                                            uint32_t b0, uint32_t p0, int16_t *dst)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t v = lane & 15;
+    const uint32_t hdr0 = 32 * a.MW;
+    for (uint32_t i = warp * 2 + (lane >> 4); i < count; i += 2 * kWarps) {
+        const uint2 it = m.list[i];
+        const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16, rank = it.y;
+        const uint32_t loc = r / 3, c = r - 3 * loc;
+        const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
+        const BlockHeader h = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
+        const uint32_t u = bise_value(rec, m.off[r * a.pmax + rank], s_mode[h.mode], v);
+        dst[((p - p0) * 48 + c * 16 + v) * kStrip + loc] = (int16_t)((h.min + (int32_t)u) * (1 << (a.q + h.shift)));
+    }
+}
 
 template <bool kPacked>
 __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
 {
     constexpr uint32_t kRowBytes = kPacked ? kStrip * 16 : kStrip * 12;
     __shared__ uint32_t s_mode[kNumModes];
+    __shared__ uint32_t s_count;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bx0 = blockIdx.x * kStrip, by = blockIdx.y;
     const uint32_t nl = min((uint32_t)kStrip, a.nlx - bx0);
     const uint32_t b0 = by * a.nlx + bx0;
-
-    uint32_t *s_node = reinterpret_cast<uint32_t *>(g_smem);
-    int16_t *s_top = reinterpret_cast<int16_t *>(s_node + a.node_words);       // [n_top][48][kStrip]
-    int16_t *s_int = s_top + (size_t)a.n_top * 48 * kStrip;                     // [n_int][48][kStrip]
-    int16_t *s_leaf = s_int + (size_t)a.n_int * 48 * kStrip;                    // [batch][48][kStrip]
-    uint8_t *s_rgb = reinterpret_cast<uint8_t *>(s_leaf + kLeafBatch * 48 * kStrip);  // [batch*4][kRowBytes]
-    uint32_t *s_words = reinterpret_cast<uint32_t *>(s_rgb + kLeafBatch * 4 * kStrip * 16);
+    const Smem m = carve(a);
 
     if (tid < kNumModes)
         s_mode[tid] = c_modes[tid];
     for (uint32_t i = tid; i < a.S; i += kThreads)
-        s_node[i] = a.node_info[i];
-    for (uint32_t i = tid; i < a.n_top * nl * 48; i += kThreads) {
-        const uint32_t t = i / (nl * 48), r = i - t * nl * 48, loc = r / 48, cv = r - loc * 48;
-        s_top[(t * 48 + cv) * kStrip + loc] = a.top[((size_t)t * a.nloc + b0 + loc) * 48 + cv];
+        m.node[i] = a.node_info[i];
+    for (uint32_t i = tid; i < a.n_top * kStrip * 48; i += kThreads) {
+        const uint32_t t = i / (kStrip * 48), rest = i - t * kStrip * 48, loc = rest / 48, cv = rest - loc * 48;
+        m.top[(t * 48 + cv) * kStrip + loc] = loc < nl ? a.top[((size_t)t * a.nloc + b0 + loc) * 48 + cv] : 0;
     }
-    const uint32_t w_begin = a.offsets[3 * b0], w_end = a.offsets[3 * (b0 + nl)];
-    const uint32_t base = w_begin & ~3u;
-    const uint32_t n16 = (w_end + 2 - base + 3) / 4;
-    const bool staged = n16 * 4 <= a.stage_words;
-    if (staged) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.records) + base / 4;
-        uint4 *dst = reinterpret_cast<uint4 *>(s_words);
-        for (uint32_t i = tid; i < n16; i += kThreads)
-            dst[i] = src[i];
+    for (uint32_t i = tid; i < a.n_int * 48 * kStrip / 2; i += kThreads)
+        reinterpret_cast<uint32_t *>(m.inter)[i] = 0;
+    __syncthreads();
+
+    // ---- phase 1: per record, the payload offset of every stored block
+    const uint32_t hdr0 = 32 * a.MW;
+    for (uint32_t r = warp; r < kRecs; r += kWarps) {
+        const uint32_t loc = r / 3;
+        uint32_t *mk = m.mask + r * a.MW;
+        if (loc >= nl) {
+            for (uint32_t w = lane; w < a.MW; w += 32)
+                mk[w] = 0;
+            continue;
+        }
+        const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
+        uint32_t P = 0;
+        for (uint32_t w0 = 0; w0 < a.MW; w0 += 32) {
+            const uint32_t word = w0 + lane < a.MW ? rec[w0 + lane] : 0u;
+            if (w0 + lane < a.MW)
+                mk[w0 + lane] = word;
+            P += __reduce_add_sync(kFullMask, (uint32_t)__popc(word));
+        }
+        uint32_t run = hdr0 + kHdrBits * P;
+        for (uint32_t h0 = 0; h0 < P; h0 += 32) {
+            const uint32_t h = h0 + lane;
+            const uint32_t len = h < P ? mode_bits(s_mode[get_bits(rec, hdr0 + kHdrBits * h, 5)]) : 0u;
+            const uint32_t incl = warp_inclusive_scan(len, lane);
+            if (h < P)
+                m.off[r * a.pmax + h] = run + incl - len;
+            run += __shfl_sync(kFullMask, incl, 31);
+        }
     }
     __syncthreads();
 
-    const bool walker = warp < 3 && (uint32_t)lane < nl;
-    const uint32_t c = warp;
-    const uint32_t *rec = nullptr;
-    uint32_t hdr_pos = 0, pay_pos = 0;
-    if (walker) {
-        const uint32_t w0 = a.offsets[3 * (b0 + lane) + c];
-        rec = staged ? s_words + (w0 - base) : a.records + w0;
-        uint32_t P = 0;
-        for (uint32_t m = 0; m < a.MW; m++)
-            P += __popc(rec[m]);
-        hdr_pos = 32 * a.MW;
-        pay_pos = hdr_pos + kHdrBits * P;
-    }
-
-    // levels >= 1 first (BFS order lists them before the views)
-    if (walker) {
-        for (uint32_t p = 0; p < a.n_int; p++) {
-            int32_t v[kVals];
-            decode_node(rec, p, hdr_pos, pay_pos, s_mode, a.q, v);
-            const uint32_t info = s_node[p];
-            const uint32_t par = node_parent(info);
-            const int16_t *src = (node_level(info) + 2 == a.L ? s_top : s_int) + (par * 48 + c * 16) * kStrip;
-            int16_t *dst = s_int + (p * 48 + c * 16) * kStrip;
-#pragma unroll
-            for (int k = 0; k < kVals; k++)
-                dst[k * kStrip + lane] = (int16_t)(src[k * kStrip + lane] + v[k]);
+    // ---- phase 2: internal nodes, decoded, then reconstructed level by level
+    if (a.n_int > 0) {
+        const uint32_t cnt = build_list(a, m, 0, a.n_int, &s_count, false);
+        decode_list(a, m, s_mode, cnt, b0, 0, m.inter);
+        __syncthreads();
+        for (uint32_t p0 = 0; p0 < a.n_int;) {
+            const uint32_t lvl = node_level(m.node[p0]);
+            uint32_t p1 = p0;
+            while (p1 < a.n_int && node_level(m.node[p1]) == lvl)
+                p1++;
+            const bool from_top = lvl + 2 == a.L;
+            for (uint32_t i = tid; i < (p1 - p0) * 48 * kStrip; i += kThreads) {
+                const uint32_t p = p0 + i / (48 * kStrip), rest = i % (48 * kStrip);
+                const uint32_t par = node_parent(m.node[p]);
+                const int16_t *src = from_top ? m.top : m.inter;
+                m.inter[p * 48 * kStrip + rest] += src[par * 48 * kStrip + rest];
+            }
+            __syncthreads();
+            p0 = p1;
         }
     }
 
-    const bool fast_rows = a.out_aligned16 && (a.W % (kPacked ? 4 : 16) == 0) && nl == kStrip && bx0 * 4 + kStrip * 4 <= a.W;
+    // ---- phase 3: the views, kLeafBatch at a time
+    const bool fast_rows = a.out_aligned16 && (a.W % (kPacked ? 4 : 16) == 0) && nl == kStrip &&
+                           bx0 * 4 + kStrip * 4 <= a.W;
     for (uint32_t p0 = a.n_int; p0 < a.S; p0 += kLeafBatch) {
         const uint32_t nb = min((uint32_t)kLeafBatch, a.S - p0);
-        if (walker) {
-            for (uint32_t j = 0; j < nb; j++) {
-                const uint32_t p = p0 + j;
-                const uint32_t info = s_node[p];
-                if (kPacked && a.needed && !a.needed[node_view(info)]) {
-                    skip_node(rec, p, hdr_pos, pay_pos, s_mode);
-                    continue;
-                }
-                int32_t v[kVals];
-                decode_node(rec, p, hdr_pos, pay_pos, s_mode, a.q, v);
-                const uint32_t par = node_parent(info);
-                const int16_t *src = (node_level(info) + 2 == a.L ? s_top : s_int) + (par * 48 + c * 16) * kStrip;
-                int16_t *dst = s_leaf + (j * 48 + c * 16) * kStrip;
-#pragma unroll
-                for (int k = 0; k < kVals; k++)
-                    dst[k * kStrip + lane] = (int16_t)(src[k * kStrip + lane] + v[k]);
-            }
-        }
+        for (uint32_t i = tid; i < kLeafBatch * 48 * kStrip / 2; i += kThreads)
+            reinterpret_cast<uint32_t *>(m.res)[i] = 0;
+        const uint32_t cnt = build_list(a, m, p0, p0 + nb, &s_count, kPacked && a.needed != nullptr);
+        decode_list(a, m, s_mode, cnt, b0, p0, m.res);
         __syncthreads();
-        // YCoCg-R -> RGB, one (leaf, pixel row) per warp iteration, lane = location
-        for (uint32_t job = warp; job < nb * 4; job += kThreads / 32) {
+        // parent + residual -> RGB, one (leaf, pixel row) per warp step;
+        // lane = (location, pixel pair)
+        for (uint32_t job = warp; job < nb * 4; job += kWarps) {
             const uint32_t j = job >> 2, row = job & 3;
-            const uint32_t view = node_view(s_node[p0 + j]);
+            const uint32_t info = m.node[p0 + j];
+            const uint32_t view = node_view(info);
             if (kPacked && a.needed && !a.needed[view])
                 continue;
-            uint8_t *srow = s_rgb + job * kRowBytes;
-            if ((uint32_t)lane < nl) {
-                uint32_t px[4];
+            const uint32_t par = node_parent(info);
+            const int16_t *base = (a.L == 2 ? m.top : m.inter) + par * 48 * kStrip;
+            const int16_t *rs = m.res + j * 48 * kStrip;
+            uint8_t *srow = m.rgb + job * kRowBytes;
+            const uint32_t loc = lane >> 1, x2 = (lane & 1) * 2;
+            if (loc < nl) {
+                uint32_t px[2];
 #pragma unroll
-                for (int x = 0; x < 4; x++) {
-                    const uint32_t k = row * 4 + x;
-                    const int16_t *lv = s_leaf + j * 48 * kStrip;
-                    px[x] = ycocg_to_rgb24(lv[k * kStrip + lane], lv[(16 + k) * kStrip + lane],
-                                           lv[(32 + k) * kStrip + lane]);
+                for (int x = 0; x < 2; x++) {
+                    const uint32_t k = row * 4 + x2 + x;
+                    const int yy = base[k * kStrip + loc] + rs[k * kStrip + loc];
+                    const int co = base[(16 + k) * kStrip + loc] + rs[(16 + k) * kStrip + loc];
+                    const int cg = base[(32 + k) * kStrip + loc] + rs[(32 + k) * kStrip + loc];
+                    px[x] = ycocg_to_rgb24(yy, co, cg);
                 }
                 if (kPacked) {
-                    reinterpret_cast<uint4 *>(srow)[lane] = make_uint4(px[0], px[1], px[2], px[3]);
+                    reinterpret_cast<uint2 *>(srow)[lane] = make_uint2(px[0], px[1]);
                 } else {
-                    uint32_t *w = reinterpret_cast<uint32_t *>(srow + lane * 12);
-                    w[0] = px[0] | (px[1] << 24);
-                    w[1] = (px[1] >> 8) | (px[2] << 16);
-                    w[2] = (px[2] >> 16) | (px[3] << 8);
+                    uint16_t *w = reinterpret_cast<uint16_t *>(srow + lane * 6);
+                    w[0] = (uint16_t)px[0];
+                    w[1] = (uint16_t)((px[0] >> 16) | (px[1] << 8));
+                    w[2] = (uint16_t)(px[1] >> 8);
                 }
             }
             __syncwarp();
@@ -201,7 +280,8 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
                     uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)view * a.H + y) * a.W + x0;
                     const uint32_t *src = reinterpret_cast<const uint32_t *>(srow);
                     if (fast_rows) {
-                        reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(src)[lane];
+                        if (lane < kStrip)
+                            reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(src)[lane];
                     } else {
                         const uint32_t npx = min(nl * 4, a.W - x0);
                         for (uint32_t b = lane; b < npx; b += 32)
@@ -225,10 +305,6 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
     }
 }
 
-}  // namespace
-
-namespace {
-
 template <bool kPacked>
 int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, cudaStream_t st)
 {
@@ -251,18 +327,13 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.W = s->info.W;
     a.H = s->info.H;
     a.out_aligned16 = ((uintptr_t)d_out & 15u) == 0;
-    a.node_words = (t.S + 3) & ~3u;
-    const size_t fixed = 4ull * a.node_words + 2ull * (t.n_top + t.n_int + kLeafBatch) * 48 * kStrip +
-                         (size_t)kLeafBatch * 4 * kStrip * 16;
-    if (fixed + 1024 > kSmemBudget) {
+    a.pmax = std::max<uint32_t>(s->max_present, 1);
+    a.list_cap = kRecs * std::max<uint32_t>(t.n_int, kLeafBatch);
+    const size_t smem = smem_bytes(a.S, a.n_top, a.n_int, a.MW, a.pmax, a.list_cap);
+    if (smem > kSmemBudget || a.S >= 65536) {
         set_error("tree too large for the decode-all kernel's shared memory");
         return RLFC_E_UNSUPPORTED;
     }
-    // stage whole strips when they fit (the largest strip plus alignment slack)
-    const size_t want = (size_t)s->max_strip_words + 8;
-    const size_t room = (kSmemBudget - fixed) / 16 * 4;
-    a.stage_words = (uint32_t)std::min(room, (want + 3) & ~size_t(3));
-    const size_t smem = fixed + 4ull * a.stage_words;
     cudaError_t e = cudaFuncSetAttribute(decode_all_kernel<kPacked>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)

@@ -113,7 +113,7 @@ int fmt(const std::string &m)
 struct Parsed {
     uint32_t U, V, W, H, B, L, q, n_top, S;
     uint64_t off_top, off_offsets, off_records, record_words;
-    uint32_t Wp, Hp, nlx, nly, nloc, MW, max_record_words, max_strip_words;
+    uint32_t Wp, Hp, nlx, nly, nloc, MW, max_record_words, max_strip_words, max_present;
     Tables tab;
 };
 
@@ -186,6 +186,7 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
     // offsets and records
     ps.MW = (ps.S + 31) / 32;
     ps.max_record_words = 0;
+    ps.max_present = 0;
     const uint8_t *off = p + ps.off_offsets;
     const uint8_t *rec = p + ps.off_records;
     if (rd32(off) != 0 || rd32(off + 4 * (noff - 1)) != ps.record_words)
@@ -207,6 +208,7 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
                     return fmt("presence bits beyond the last node");
             P += __builtin_popcount(w);
         }
+        ps.max_present = std::max(ps.max_present, P);
         uint64_t bits = 32ull * ps.MW + 18ull * P;
         if (bits > 32ull * words)
             return fmt("block headers run past the record");
@@ -282,6 +284,7 @@ int load(const uint8_t *bytes, size_t nbytes, cudaStream_t st, rlfc_stream **out
     s->record_words = ps.record_words;
     s->max_record_words = ps.max_record_words;
     s->max_strip_words = ps.max_strip_words;
+    s->max_present = ps.max_present;
     rlfc_info &in = s->info;
     in.U = ps.U; in.V = ps.V; in.W = ps.W; in.H = ps.H; in.B = ps.B; in.L = ps.L; in.q = ps.q;
     in.n_top = ps.n_top; in.S = ps.S; in.Wp = ps.Wp; in.Hp = ps.Hp;
