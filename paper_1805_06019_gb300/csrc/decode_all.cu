@@ -7,9 +7,10 @@
 //     presence mask) and turns the closed-form payload lengths of their
 //     headers into payload offsets with a warp scan;
 //  2. internal nodes (levels >= 1, first in BFS order): the stored blocks are
-//     compacted into a work list and decoded lane-per-value by half-warps
-//     (no lane idles on an absent node), then the levels are added top-down:
-//     reconstruction = parent reconstruction (or top RKV) + residual;
+//     compacted into a work list (no thread idles on an absent node) and each
+//     thread decodes whole blocks with a sequential bit reader; the levels are
+//     then added top-down: reconstruction = parent reconstruction (or top
+//     RKV) + residual;
 //  3. the views (leaves), kLeafBatch at a time: compacted, decoded the same
 //     way into a residual buffer, then parent + residual is converted from
 //     YCoCg-R to RGB and written as whole image rows with 16-byte stores.
@@ -32,7 +33,7 @@ namespace {
 constexpr int kStrip = 16;       // block locations per CTA
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kLeafBatch = 8;
+constexpr int kLeafBatch = 16;
 constexpr int kRecs = 3 * kStrip;
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
@@ -57,7 +58,7 @@ struct Smem {
     int16_t *top;      // [n_top][48][kStrip]
     int16_t *inter;    // [n_int][48][kStrip]  internal reconstructions
     int16_t *res;      // [kLeafBatch][48][kStrip]  leaf residuals
-    uint8_t *rgb;      // [kLeafBatch * 4][row bytes]
+    uint8_t *rgb;      // [kWarps][row bytes]: one output row per warp
     uint32_t *mask;    // [kRecs][MW]
     uint32_t *off;     // [kRecs][pmax]  payload bit offset of each stored block
     uint2 *list;       // [list_cap]  (node | record << 16, rank)
@@ -80,7 +81,7 @@ __device__ __forceinline__ Smem carve(const Args &a)
     m.res = reinterpret_cast<int16_t *>(p);
     p += r16(2ull * kLeafBatch * 48 * kStrip);
     m.rgb = p;
-    p += r16((size_t)kLeafBatch * 4 * kStrip * 16);
+    p += r16((size_t)kWarps * kStrip * 16);
     m.mask = reinterpret_cast<uint32_t *>(p);
     p += r16(4ull * kRecs * a.MW);
     m.off = reinterpret_cast<uint32_t *>(p);
@@ -92,7 +93,7 @@ __device__ __forceinline__ Smem carve(const Args &a)
 inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap)
 {
     return r16(4ull * S) + r16(2ull * n_top * 48 * kStrip) + r16(2ull * n_int * 48 * kStrip) +
-           r16(2ull * kLeafBatch * 48 * kStrip) + r16((size_t)kLeafBatch * 4 * kStrip * 16) +
+           r16(2ull * kLeafBatch * 48 * kStrip) + r16((size_t)kWarps * kStrip * 16) +
            r16(4ull * kRecs * MW) + r16(4ull * kRecs * pmax) + r16(8ull * list_cap);
 }
 
@@ -135,23 +136,26 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
     return *s_count;
 }
 
-// Decode the listed blocks, a half-warp per block, lane = value; the
-// residual (min + u) * 2^(q + shift) goes to the node's slot in dst:
+// Decode the listed blocks, one block per thread; the residual
+// (min + u) * 2^(q + shift) goes to the node's slot in dst:
 // dst[((node - p0) * 48 + channel * 16 + value) * kStrip + location].
 __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
                                             uint32_t b0, uint32_t p0, int16_t *dst)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t v = lane & 15;
     const uint32_t hdr0 = 32 * a.MW;
-    for (uint32_t i = warp * 2 + (lane >> 4); i < count; i += 2 * kWarps) {
+    for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         const uint2 it = m.list[i];
         const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16, rank = it.y;
         const uint32_t loc = r / 3, c = r - 3 * loc;
         const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
         const BlockHeader h = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
-        const uint32_t u = bise_value(rec, m.off[r * a.pmax + rank], s_mode[h.mode], v);
-        dst[((p - p0) * 48 + c * 16 + v) * kStrip + loc] = (int16_t)((h.min + (int32_t)u) * (1 << (a.q + h.shift)));
+        int32_t u[kVals];
+        bise_decode16(rec, m.off[r * a.pmax + rank], s_mode[h.mode], u);
+        const int32_t scale = 1 << (a.q + h.shift);
+        int16_t *d = dst + ((p - p0) * 48 + c * 16) * kStrip + loc;
+#pragma unroll
+        for (int v = 0; v < kVals; v++)
+            d[v * kStrip] = (int16_t)((h.min + u[v]) * scale);
     }
 }
 
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
             const uint32_t par = node_parent(info);
             const int16_t *base = (a.L == 2 ? m.top : m.inter) + par * 48 * kStrip;
             const int16_t *rs = m.res + j * 48 * kStrip;
-            uint8_t *srow = m.rgb + job * kRowBytes;
+            uint8_t *srow = m.rgb + warp * kRowBytes;
             const uint32_t loc = lane >> 1, x2 = (lane & 1) * 2;
             if (loc < nl) {
                 uint32_t px[2];
