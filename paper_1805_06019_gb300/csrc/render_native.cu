@@ -26,6 +26,7 @@
 //  4. per view, each thread blends one column of 4 pixels, sliding a 2 x 2
 //     stencil down the window (lanes read consecutive words, no bank
 //     conflicts), and writes with streaming stores.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -125,16 +126,26 @@ struct Window {
 // and integer shifts.
 struct ViewP {
     float w[4][4];            // [k][00, 10, 01, 11]
+    int base[4];              // sample (0, 0) of the view's 2 x 2 stencil in window k
     int16_t ox[4], oy[4];
+    uint32_t used;            // bit k: neighbour k has a non-zero weight
 };
 
 extern __shared__ __align__(16) uint32_t g_dyn[];
 
-// Shared-memory words of the four neighbours' windows for a tile of tw x th
-// pixels with the given shift spreads, plus the per-location node table.
+// Shared-memory words of one neighbour's window (two words per pixel) for a
+// tile of tw x th pixels with the given shift spreads.
 __host__ __device__ __forceinline__ uint32_t window_words(int tw, int th, int sx, int sy)
 {
-    return (uint32_t)(tw + 2 + sx) * (uint32_t)(th + 1 + sy);
+    return 2u * (uint32_t)(tw + 2 + sx) * (uint32_t)(th + 1 + sy);
+}
+
+// A window pixel: R, G and B as halves (8-bit values are exact in fp16).
+__device__ __forceinline__ uint2 rgb_half(uint32_t rgb24)
+{
+    const __half2 rg = __floats2half2_rn((float)(rgb24 & 255u), (float)((rgb24 >> 8) & 255u));
+    const __half2 b0 = __floats2half2_rn((float)((rgb24 >> 16) & 255u), 0.0f);
+    return make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
 }
 
 // One out-of-line copy of the block decoder keeps the kernel's code small
@@ -149,12 +160,6 @@ __device__ __noinline__ void decode_block_values(const uint32_t *rec, uint32_t p
         acc[v] += (mn + u[v]) * scale;
 }
 
-// Exact float of byte c of a packed RGB word: 2^23 + byte, built with one
-// byte permute, minus 2^23.
-__device__ __forceinline__ float byte_to_float(uint32_t p, int c)
-{
-    return __int_as_float((int)__byte_perm(p, 0x4Bu, (uint32_t)c | 0x4650u)) - 8388608.0f;
-}
 
 __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a)
 {
@@ -220,12 +225,30 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     vp.w[k][3] = wk * sh[k].fx * sh[k].fy;
                     vp.ox[k] = (int16_t)sh[k].ox;
                     vp.oy[k] = (int16_t)sh[k].oy;
-                    atomicMin(&s_oxmin[k], sh[k].ox);
-                    atomicMax(&s_oxmax[k], sh[k].ox);
-                    atomicMin(&s_oymin[k], sh[k].oy);
-                    atomicMax(&s_oymax[k], sh[k].oy);
+                    if (k == 0)
+                        vp.used = 0;
                     if (w[k] != 0.0f)
-                        atomicOr(&s_used[k], 1);
+                        vp.used |= 1u << k;
+                }
+            }
+            if (tid < kGroupCap) {
+                // group extents per neighbour: warp reductions, one atomic per warp
+                const bool mine = tid < gcap;
+                const ViewP &vp = s_vp[mine ? tid : 0];
+                for (int k = 0; k < 4; k++) {
+                    const int lo_x = __reduce_min_sync(kFullMask, mine ? (int)vp.ox[k] : INT_MAX);
+                    const int hi_x = __reduce_max_sync(kFullMask, mine ? (int)vp.ox[k] : INT_MIN);
+                    const int lo_y = __reduce_min_sync(kFullMask, mine ? (int)vp.oy[k] : INT_MAX);
+                    const int hi_y = __reduce_max_sync(kFullMask, mine ? (int)vp.oy[k] : INT_MIN);
+                    const unsigned used = __reduce_or_sync(kFullMask, mine ? (vp.used >> k) & 1u : 0u);
+                    if ((tid & 31) == 0 && (tid < gcap)) {
+                        atomicMin(&s_oxmin[k], lo_x);
+                        atomicMax(&s_oxmax[k], hi_x);
+                        atomicMin(&s_oymin[k], lo_y);
+                        atomicMax(&s_oymax[k], hi_y);
+                        if (used)
+                            atomicOr(&s_used[k], 1);
+                    }
                 }
             }
             __syncthreads();
@@ -305,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     wn.cy0 = min(max(wn.wy0, 0), (int)a.H - 1);
                     wn.cy1 = min(max(wn.wy0 + wn.WY - 1, 0), (int)a.H - 1);
                     wn.f_off = off;
-                    off += (uint32_t)(wn.FW * wn.WY);
+                    off += 2u * (uint32_t)(wn.FW * wn.WY);
                     if (s_used[k]) {
                         bx0 = min(bx0, wn.cx0 / kBlock);
                         by0 = min(by0, wn.cy0 / kBlock);
@@ -318,9 +341,10 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                 s_rect[2] = bx1 - bx0 + 1;
                 s_rect[3] = by1 - by0 + 1;
                 s_ent_off = (off + 3) & ~3u;
-                // BFS positions the used neighbours need, ascending
+                // BFS positions the used neighbours need, ascending (only
+                // when decoding here)
                 int nn = 0;
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < 4 && !a.decoded; k++) {
                     const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
                     s_top[k] = anc[a.sv.L - 1];
                     if (!s_used[k])
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         s_need_pos[y] = s_need_pos[y - 1];
                         s_need_pos[y - 1] = tp;
                     }
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < 4 && !a.decoded; k++) {
                     const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
                     for (uint32_t l = 0; l + 1 < a.sv.L; l++) {
                         int e = -1;
@@ -354,6 +378,11 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
             }
             __syncthreads();
             const int ge = s_gend;
+            if (tid < ge - g0) {
+                ViewP &vp = s_vp[tid];
+                for (int k = 0; k < 4; k++)
+                    vp.base[k] = (vp.oy[k] - s_win[k].oymin) * s_win[k].FW + (vp.ox[k] - s_win[k].oxmin);
+            }
             const int nbx = s_rect[2], nloc_r = nbx * s_rect[3];
             const int nn = s_nneed;
             // node table entry (2 words) of needed node e at union location li, channel c:
@@ -363,17 +392,33 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
 
             if (a.decoded) {
                 // ---- phase 2 (decoded views): copy the windows, clamped to the image
-                for (int k = 0; k < 4; k++) {
-                    if (!s_used[k])
-                        continue;
+                // one warp per window row, three independent loads per lane
+                const int lane = tid & 31, warp = tid >> 5;
+                int rows = 0;
+                for (int k = 0; k < 4; k++)
+                    rows += s_used[k] ? s_win[k].WY : 0;
+                for (int rr = warp; rr < rows; rr += kThreads / 32) {
+                    int k = 0, r = rr;
+                    while (!s_used[k] || r >= s_win[k].WY) {
+                        r -= s_used[k] ? s_win[k].WY : 0;
+                        k++;
+                    }
                     const Window &wn = s_win[k];
-                    const uint32_t *img = a.decoded + (size_t)nview[k] * a.W * a.H;
-                    uint32_t *f = g_dyn + wn.f_off;
-                    for (int i = tid; i < wn.WX * wn.WY; i += kThreads) {
-                        const int r = i / wn.WX, cc = i - r * wn.WX;
-                        const int gx = min(max(wn.wx0 + cc, 0), (int)a.W - 1);
-                        const int gy = min(max(wn.wy0 + r, 0), (int)a.H - 1);
-                        f[r * wn.FW + cc] = __ldg(img + (size_t)gy * a.W + gx);
+                    const uint32_t *src = a.decoded + ((size_t)nview[k] * a.H + min(max(wn.wy0 + r, 0), (int)a.H - 1)) * a.W;
+                    uint2 *dst = reinterpret_cast<uint2 *>(g_dyn + wn.f_off) + r * wn.FW;
+                    for (int c0 = 0; c0 < wn.WX; c0 += 96) {
+                        uint32_t v[3];
+#pragma unroll
+                        for (int j = 0; j < 3; j++) {
+                            const int cc = c0 + lane + 32 * j;
+                            v[j] = cc < wn.WX ? __ldg(src + min(max(wn.wx0 + cc, 0), (int)a.W - 1)) : 0u;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 3; j++) {
+                            const int cc = c0 + lane + 32 * j;
+                            if (cc < wn.WX)
+                                dst[cc] = rgb_half(v[j]);
+                        }
                     }
                 }
                 __syncthreads();
@@ -456,15 +501,16 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     for (int v = 0; v < kVals; v += 2)
                         pk[c][v >> 1] = ((uint32_t)acc[v] & 0xFFFFu) | ((uint32_t)acc[v + 1] << 16);
                 }
-                uint32_t *f = g_dyn + wn.f_off;
+                uint2 *f = reinterpret_cast<uint2 *>(g_dyn + wn.f_off);
 #pragma unroll
                 for (int v = 0; v < kVals; v++) {
                     const int px = bx * kBlock + (v & 3), py = by * kBlock + (v >> 2);
                     if (px < wn.cx0 || px > wn.cx1 || py < wn.cy0 || py > wn.cy1)
                         continue;
                     const int sh16 = 16 * (v & 1);
-                    const uint32_t rgb = ycocg_to_rgb24((int16_t)(pk[0][v >> 1] >> sh16), (int16_t)(pk[1][v >> 1] >> sh16),
-                                                        (int16_t)(pk[2][v >> 1] >> sh16));
+                    const uint2 rgb = rgb_half(ycocg_to_rgb24((int16_t)(pk[0][v >> 1] >> sh16),
+                                                              (int16_t)(pk[1][v >> 1] >> sh16),
+                                                              (int16_t)(pk[2][v >> 1] >> sh16)));
                     // window columns whose clamped x is px (more than one on the image edge)
                     const int xa = (px == 0 ? wn.wx0 : px) - wn.wx0, xb = (px == (int)a.W - 1 ? wn.wx0 + wn.WX - 1 : px) - wn.wx0;
                     const int ya = (py == 0 ? wn.wy0 : py) - wn.wy0, yb = (py == (int)a.H - 1 ? wn.wy0 + wn.WY - 1 : py) - wn.wy0;
@@ -490,32 +536,38 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
 #pragma unroll 1
                 for (int k = 0; k < 4; k++) {
-                    const float w00 = vp.w[k][0], w10 = vp.w[k][1], w01 = vp.w[k][2], w11 = vp.w[k][3];
-                    if (w00 == 0.0f && w10 == 0.0f && w01 == 0.0f && w11 == 0.0f)
+                    if (!((vp.used >> k) & 1u))
                         continue;
-                    const Window &wn = s_win[k];
-                    const uint32_t *f = g_dyn + wn.f_off + (r0 + vp.oy[k] - wn.oymin) * wn.FW + (col + vp.ox[k] - wn.oxmin);
+                    const float w00 = vp.w[k][0], w10 = vp.w[k][1], w01 = vp.w[k][2], w11 = vp.w[k][3];
+                    const int fw = s_win[k].FW;
+                    const uint2 *f = reinterpret_cast<const uint2 *>(g_dyn + s_win[k].f_off) + vp.base[k] + r0 * fw + col;
                     float a0[3], a1[3];
                     {
-                        const uint32_t p0 = f[0], p1 = f[1];
-#pragma unroll
-                        for (int ch = 0; ch < 3; ch++) {
-                            a0[ch] = byte_to_float(p0, ch);
-                            a1[ch] = byte_to_float(p1, ch);
-                        }
+                        const uint2 p0 = f[0], p1 = f[1];
+                        const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&p0.x));
+                        const float2 rg1 = __half22float2(*reinterpret_cast<const __half2 *>(&p1.x));
+                        a0[0] = rg0.x;
+                        a0[1] = rg0.y;
+                        a0[2] = __low2float(*reinterpret_cast<const __half2 *>(&p0.y));
+                        a1[0] = rg1.x;
+                        a1[1] = rg1.y;
+                        a1[2] = __low2float(*reinterpret_cast<const __half2 *>(&p1.y));
                     }
 #pragma unroll
                     for (int rr = 0; rr < kRows; rr++) {
                         if (r0 + rr >= th)
                             break;   // the window holds rows up to th + spread only
-                        f += wn.FW;
-                        const uint32_t p0 = f[0], p1 = f[1];
+                        f += fw;
+                        const uint2 p0 = f[0], p1 = f[1];
+                        const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&p0.x));
+                        const float2 rg1 = __half22float2(*reinterpret_cast<const __half2 *>(&p1.x));
+                        const float b0[3] = {rg0.x, rg0.y, __low2float(*reinterpret_cast<const __half2 *>(&p0.y))};
+                        const float b1[3] = {rg1.x, rg1.y, __low2float(*reinterpret_cast<const __half2 *>(&p1.y))};
 #pragma unroll
                         for (int ch = 0; ch < 3; ch++) {
-                            const float b0 = byte_to_float(p0, ch), b1 = byte_to_float(p1, ch);
-                            acc[rr][ch] += w00 * a0[ch] + w10 * a1[ch] + w01 * b0 + w11 * b1;
-                            a0[ch] = b0;
-                            a1[ch] = b1;
+                            acc[rr][ch] += w00 * a0[ch] + w10 * a1[ch] + w01 * b0[ch] + w11 * b1[ch];
+                            a0[ch] = b0[ch];
+                            a1[ch] = b1[ch];
                         }
                     }
                 }
