@@ -40,6 +40,12 @@ METRIC = "decoded Mpix/s and % HBM roofline; 512×512 views/s; served p50/p99 vi
 UNIT = "Mpix/s"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
+# capture of the same kernel build on this workload (config, tau, views,
+# kernel); a kernel missing here reports null
+TRAFFIC_PER_LAUNCH = {}
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -142,6 +148,57 @@ def _algorithmic_bytes(info, n_views_lf, n_render, out_w, out_h):
     return decode, render, stream_read
 
 
+def _needed_views(cams, U, V):
+    """Grid views the renderer blends for these cameras: the 2 x 2 neighbours
+    of each clamped camera position."""
+    need = set()
+    for u, v, _ in cams:
+        cu, cv = min(max(float(u), 0.0), U - 1.0), min(max(float(v), 0.0), V - 1.0)
+        i0 = min(int(cu), max(U - 2, 0))
+        j0 = min(int(cv), max(V - 2, 0))
+        for j in (j0, min(j0 + 1, V - 1)):
+            for i in (i0, min(i0 + 1, U - 1)):
+                need.add(j * U + i)
+    return len(need)
+
+
+def _kernel_bytes(info, stream_read, n_views_lf, n_needed, n_render, out_w, out_h):
+    """Algorithmic bytes of one launch of each library kernel on this
+    workload: what the step it implements must read and write at least."""
+    px_view = info.W * info.H
+    out_px = n_render * out_w * out_h
+    return {
+        # compressed stream read once, RGB8 written
+        "decode_all_kernel": stream_read + 3 * px_view * n_views_lf,
+        # the views the renderer needs, as one 32-bit RGB word per pixel
+        "decode_all_kernel<packed>": stream_read + 4 * px_view * n_needed,
+        # camera table read, one mask byte per view written
+        "mark_needed_kernel": 12 * n_render + n_views_lf,
+        # decoded neighbour views read once, float RGB written
+        "render_native_kernel": 4 * px_view * n_needed + 12 * out_px,
+        "render_tiled_kernel": stream_read + 12 * out_px,
+        "render_direct_kernel": stream_read + 12 * out_px,
+    }
+
+
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    replica sets the job's time); identity on one rank."""
+    if world <= 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_mpix_per_s(world, px_per_rank, ms):
+    """Whole-job throughput: every replica processes px_per_rank pixels per
+    step, the step lasting the slowest rank's ms."""
+    return world * px_per_rank / (ms * 1e-3) / 1e6
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -189,6 +246,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    rlfc.trace_read(reset=True)
+    rlfc.trace_enable(True)
     for k in range(args.steps):
         flush.fill_(k & 255)
         a, b, c = evs[k]
@@ -201,20 +260,18 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    trace = rlfc.trace_read(reset=True)
+    rlfc.trace_enable(False)
     t_dec = [a.elapsed_time(b) for a, b, _ in evs]
     t_ren = [b.elapsed_time(c) for _, b, c in evs]
     step_ms = sum(t_dec) / args.steps + sum(t_ren) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms, sum(t_dec) / args.steps, sum(t_ren) / args.steps], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, dec_ms, ren_ms = t.tolist()
-    else:
-        dec_ms, ren_ms = sum(t_dec) / args.steps, sum(t_ren) / args.steps
+    step_ms, dec_ms, ren_ms = max_over_ranks([step_ms, sum(t_dec) / args.steps, sum(t_ren) / args.steps],
+                                             world, "cuda")
 
     info = st.info
     px_lf = U * V * p["W"] * p["H"]
     px_render = n_render * out_w * out_h
-    value = world * (px_lf + px_render) / (step_ms * 1e-3) / 1e6
+    value = job_mpix_per_s(world, px_lf + px_render, step_ms)
     peak, peak_src = _peaks()
     b_dec, b_ren, stream_read = _algorithmic_bytes(info, U * V, n_render, out_w, out_h)
     dec_gbs = b_dec / (dec_ms * 1e-3) / 1e9
@@ -225,11 +282,23 @@ def run_ours(args):
         "render": {"ms": ren_ms, "views_per_s": n_render / (ren_ms * 1e-3), "mpix_s": px_render / (ren_ms * 1e-3) / 1e6,
                    "algorithmic_bytes": b_ren, "gbs": ren_gbs, "hbm_frac": ren_gbs / peak},
     }
-    dom = "render" if ren_ms >= dec_ms else "decode_all"
-    render_kernel = "render_native_kernel" if (out_w, out_h) == (p["W"], p["H"]) else "render_tiled_kernel"
-    roof = {"bound": "hbm", "kernel": render_kernel if dom == "render" else "decode_all_kernel",
-            "achieved": parts[dom]["gbs"], "peak": peak, "unit": "GB/s", "frac": parts[dom]["gbs"] / peak,
-            "peak_source": f"{peak_src} hbm_gbs", "traffic": None}
+    # per-kernel durations from the library's own CUDA events (on the
+    # launching stream, inside the timed region); the roofline is that of the
+    # kernel with the most device time
+    n_needed = _needed_views(cams, U, V)
+    kbytes = _kernel_bytes(info, stream_read, U * V, n_needed, n_render, out_w, out_h)
+    kernels = {}
+    for name, (launches, tot) in trace.items():
+        avg = tot / max(launches, 1)
+        gbs = kbytes.get(name, 0) / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        kernels[name] = {"launches": launches, "avg_ms": avg, "share": tot / max(sum(t for _, t in trace.values()), 1e-9),
+                         "algorithmic_bytes": kbytes.get(name), "gbs": gbs, "hbm_frac": gbs / peak}
+    top = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+    roof = {"bound": "hbm", "kernel": top, "achieved": kernels[top]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kernels[top]["gbs"] / peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+            "traffic": TRAFFIC_PER_LAUNCH.get((args.config, tau, n_render, top)),
+            "bytes_per_launch": kernels[top]["algorithmic_bytes"], "avg_launch_ms": kernels[top]["avg_ms"]}
+    gpu_launches = sum(l for l, _ in trace.values())
 
     # end to end through the C ABI: per-step camera upload from pinned host
     # memory, decode + render, and download of every output to pinned memory
@@ -252,12 +321,8 @@ def run_ours(args):
             h_views.copy_(out_views, non_blocking=True)
         e1.record(cur)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / e_steps
-        if world > 1:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * (px_lf + px_render) / (e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+        e_ms = max_over_ranks([e0.elapsed_time(e1) / e_steps], world, "cuda")[0]
+        e2e = {"value": job_mpix_per_s(world, px_lf + px_render, e_ms), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h_uv.numel() * 4 + h_disp.numel() * 4),
                "d2h_bytes_per_step": int(h_lf.numel() + h_views.numel() * 4), "steps": e_steps}
 
@@ -271,8 +336,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config_json(p, n_render, out_w, out_h, tau,
                                        {"stream_bytes": int(info.stream_bytes), "parallelism": f"replicas{world}"}),
-                "parts": parts, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 2 * args.steps, "clocks": clk}
+                "parts": parts, "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clk}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -347,7 +412,7 @@ def main():
     ap.add_argument("--n-views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-views", type=int, default=50)
+    ap.add_argument("--cpu-sample-views", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

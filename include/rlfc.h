@@ -230,6 +230,25 @@ RLFC_API int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *c
 RLFC_API int rlfc_encode_no_alloc(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream,
                                   void *host_out, size_t capacity, size_t *nbytes);
 
+/*
+ * Kernel tracing (a profiling aid; the paper has no counterpart).  While
+ * tracing is on, every kernel the library launches outside stream capture is
+ * bracketed by two CUDA events on its launching stream, and the durations are
+ * summed per kernel name.  rlfc_trace_read waits for the traced work, then
+ * writes up to `cap` entries (one per kernel name seen since the last reset)
+ * and sets *n to the number of names; with reset != 0 the totals restart
+ * from zero.  Tracing adds two event records per launch; leave it off when
+ * timing whole calls.  Errors: RLFC_E_INVALID_ARG, RLFC_E_CUDA.
+ */
+typedef struct {
+    char kernel[56];     /* kernel name, NUL-terminated */
+    uint64_t launches;   /* traced launches */
+    double total_ms;     /* summed event-to-event durations */
+} rlfc_trace_entry;
+
+RLFC_API int rlfc_trace_enable(int on);
+RLFC_API int rlfc_trace_read(rlfc_trace_entry *out, size_t cap, size_t *n, int reset);
+
 /* Free a host buffer returned by the library. */
 RLFC_API void rlfc_free_host(void *p);
 

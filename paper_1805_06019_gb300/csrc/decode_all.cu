@@ -343,7 +343,7 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_all: shared memory attribute");
     dim3 grid((a.nlx + kStrip - 1) / kStrip, s->info.nloc_y);
-    decode_all_kernel<kPacked><<<grid, kThreads, smem, st>>>(a);
+    { rlfc::TraceScope trace_((kPacked ? "decode_all_kernel<packed>" : "decode_all_kernel"), st); decode_all_kernel<kPacked><<<grid, kThreads, smem, st>>>(a); }
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_all launch");

@@ -90,7 +90,7 @@ int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uin
     a.n = n;
     a.aligned = ((uintptr_t)d_out & 3u) == 0;
     const uint32_t grid = (n + kWarpsPerCta - 1) / kWarpsPerCta;
-    decode_blocks_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(a);
+    { rlfc::TraceScope trace_("decode_blocks_kernel", st); decode_blocks_kernel<<<grid, kWarpsPerCta * 32, 0, st>>>(a); }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_blocks launch");

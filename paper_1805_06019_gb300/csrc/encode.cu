@@ -466,7 +466,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     const int threads = 256;
     auto grid_for = [](size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 64); };
 
-    ycocg_pad_kernel<<<grid_for(plane * cnt[0]), threads, 0, st>>>(d_rgb, img[0], cnt[0], W, H, Wp, Hp);
+    { rlfc::TraceScope trace_("ycocg_pad_kernel", st); ycocg_pad_kernel<<<grid_for(plane * cnt[0]), threads, 0, st>>>(d_rgb, img[0], cnt[0], W, H, Wp, Hp); }
 
     // bottom-up filter
     for (uint32_t l = 1; l < L; l++) {
@@ -506,7 +506,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
         cudaMemcpyAsync(d_sh, shift.data(), 4 * shift.size(), cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(d_mw, mw.data(), 8 * mw.size(), cudaMemcpyHostToDevice, st);
         dim3 grid((unsigned)std::min<size_t>((npix + 255) / 256, 4096), cnt[l]);
-        filter_kernel<<<grid, threads, 0, st>>>(img[l - 1], img[l], d_ms, d_mi, d_mw, d_sh, npix);
+        { rlfc::TraceScope trace_("filter_kernel", st); filter_kernel<<<grid, threads, 0, st>>>(img[l - 1], img[l], d_ms, d_mi, d_mw, d_sh, npix); }
         // keep the host vectors alive until the copies are done
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(e, "encoder filter");
@@ -532,7 +532,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
         s.tau_p = p->tau_p;
         s.tau_b = p->tau_b;
         s.q = p->q;
-        srv_kernel<<<grid_for((size_t)cnt[l - 1] * 3 * nloc), threads, 0, st>>>(s);
+        { rlfc::TraceScope trace_("srv_kernel", st); srv_kernel<<<grid_for((size_t)cnt[l - 1] * 3 * nloc), threads, 0, st>>>(s); }
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(e, "encoder residuals");
     }
@@ -580,7 +580,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     ra.words = d_words_n;
     ra.offsets = nullptr;
     ra.error = d_err;
-    record_size_kernel<<<(3 * nloc + 127) / 128, 128, 0, st>>>(ra);
+    { rlfc::TraceScope trace_("record_size_kernel", st); record_size_kernel<<<(3 * nloc + 127) / 128, 128, 0, st>>>(ra); }
     std::vector<uint32_t> words(3ull * nloc), offsets(3ull * nloc + 1);
     int h_err = 0;
     cudaMemcpyAsync(words.data(), d_words_n, 4ull * 3 * nloc, cudaMemcpyDeviceToHost, st);
@@ -606,7 +606,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     cudaMemcpyAsync(d_off, offsets.data(), 4ull * offsets.size(), cudaMemcpyHostToDevice, st);
     ra.words = d_rec;
     ra.offsets = d_off;
-    record_pack_kernel<<<(3 * nloc + 127) / 128, 128, 0, st>>>(ra);
+    { rlfc::TraceScope trace_("record_pack_kernel", st); record_pack_kernel<<<(3 * nloc + 127) / 128, 128, 0, st>>>(ra); }
 
     // assemble the stream
     const size_t hdr_end = 64 + 8ull * L + 4ull * S;

@@ -309,7 +309,7 @@ int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, 
         if (e != cudaSuccess)
             return cuda_fail(e, "render: shared memory attribute");
         dim3 grid(a.tiles_x * tiles_y, n);
-        render_tiled_kernel<<<grid, kThreads, smem, st>>>(a);
+        { rlfc::TraceScope trace_("render_tiled_kernel", st); render_tiled_kernel<<<grid, kThreads, smem, st>>>(a); }
     } else {
         a.max_fp_blocks = 0;
         const uint64_t pix = (uint64_t)out_w * out_h;
@@ -318,7 +318,7 @@ int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, 
             return RLFC_E_RANGE;
         }
         dim3 grid((uint32_t)((pix + 255) / 256), n);
-        render_direct_kernel<<<grid, 256, 0, st>>>(a);
+        { rlfc::TraceScope trace_("render_direct_kernel", st); render_direct_kernel<<<grid, 256, 0, st>>>(a); }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess)

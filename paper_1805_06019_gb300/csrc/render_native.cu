@@ -663,12 +663,12 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
         if ((e = cudaMemsetAsync(needed, 0, mask_bytes, st)) != cudaSuccess)
             rc = cuda_fail(e, "render: clearing the view mask");
         if (rc == RLFC_OK) {
-            mark_needed_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, needed);
+            { rlfc::TraceScope trace_("mark_needed_kernel", st); mark_needed_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, needed); }
             rc = launch_decode_packed(s, decoded, needed, st);
         }
         if (rc == RLFC_OK) {
             a.decoded = decoded;
-            render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+            { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
             e = cudaGetLastError();
             if (e != cudaSuccess)
                 rc = cuda_fail(e, "render_native launch");
@@ -677,7 +677,7 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
         return rc;
     }
     cudaGetLastError();   // a failed stream-ordered allocation only selects the other path
-    render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "render_native launch");

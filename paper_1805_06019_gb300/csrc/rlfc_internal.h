@@ -50,6 +50,21 @@ struct rlfc_stream {
 namespace rlfc {
 
 void set_error(const std::string &msg);
+
+// Records CUDA events around the launches made during its lifetime when
+// tracing is on (rlfc_trace_enable); the name must be a string literal.
+class TraceScope {
+public:
+    TraceScope(const char *name, cudaStream_t st);
+    ~TraceScope();
+    TraceScope(const TraceScope &) = delete;
+    TraceScope &operator=(const TraceScope &) = delete;
+
+private:
+    const char *name_;
+    cudaStream_t st_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 int build_tables(uint32_t L, const std::vector<uint32_t> &cnt,
                  const std::vector<std::vector<uint32_t>> &parent, Tables &t);
 int cuda_fail(cudaError_t e, const char *what);

@@ -38,9 +38,13 @@ class EncParams(ctypes.Structure):
                 ("q", ctypes.c_uint32)]
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char * 56), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
 EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
            "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_no_alloc",
-           "rlfc_free_host", "rlfc_strerror", "rlfc_last_error"]
+           "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read"]
 
 _lib = None
 _lock = threading.Lock()
@@ -74,6 +78,8 @@ def lib():
             L.rlfc_strerror.restype = ctypes.c_char_p
             L.rlfc_last_error.argtypes = []
             L.rlfc_last_error.restype = ctypes.c_char_p
+            L.rlfc_trace_enable.argtypes = [ctypes.c_int]
+            L.rlfc_trace_read.argtypes = [ctypes.POINTER(TraceEntry), sz, ctypes.POINTER(sz), ctypes.c_int]
             _lib = L
         return _lib
 
@@ -82,6 +88,23 @@ def _check(code: int):
     if code != RLFC_OK:
         L = lib()
         raise RLFCError(code, f"{L.rlfc_strerror(code).decode()}: {L.rlfc_last_error().decode()}")
+
+
+def trace_enable(on: bool = True):
+    """Bracket every library kernel launch with CUDA events (rlfc_trace_enable)."""
+    _check(lib().rlfc_trace_enable(1 if on else 0))
+
+
+def trace_read(reset: bool = True) -> dict:
+    """{kernel name: (launches, total ms)} since the last reset, after waiting
+    for the traced work (rlfc_trace_read)."""
+    L = lib()
+    n = ctypes.c_size_t()
+    _check(L.rlfc_trace_read(None, 0, ctypes.byref(n), 0))
+    cap = max(n.value, 1)
+    arr = (TraceEntry * cap)()
+    _check(L.rlfc_trace_read(arr, cap, ctypes.byref(n), 1 if reset else 0))
+    return {arr[k].kernel.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(min(n.value, cap))}
 
 
 def _stream_handle(stream) -> int:
