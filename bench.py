@@ -401,6 +401,168 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _stream_location_words(data: bytes):
+    """Words of the three channel records of every block location, from the
+    stream's offset table (format v1 header: 16 little-endian uint32)."""
+    h = np.frombuffer(data[:64], dtype="<u4")
+    U, V, W, H, B = (int(x) for x in h[2:7])
+    nloc = ((W + B - 1) // B) * ((H + B - 1) // B)
+    off = np.frombuffer(data, dtype="<u4", count=3 * nloc + 1, offset=int(h[12]))
+    return (off[3::3] - off[0:-1:3]).astype(np.int64), nloc
+
+
+def run_batching(args):
+    """10^6 uniform random (view, location) block requests per launch on the
+    17 x 17 x 1024^2 light field: the persistent binned kernel (autotuned,
+    eager and replayed as a CUDA graph) against one warp per request, plus a
+    full decode of the same light field."""
+    import torch
+    from paper_1805_06019_gb300 import rlfc
+
+    torch.cuda.set_device(0)
+    p = lf_synth.PRESETS["batching"]
+    tau = args.tau if args.tau is not None else p["taus"][0]
+    n = args.n_requests or p["n_requests"]
+    U, V = p["U"], p["V"]
+    t0 = time.time()
+    lf = lf_synth.preset_lightfield("batching")
+    t_synth = time.time() - t0
+    d_lf = torch.from_numpy(lf).cuda()
+    data = rlfc.encode(d_lf, U, V, p["L"], p["c"], tau_p=tau, tau_b=16 * tau)
+    del d_lf
+    st = rlfc.Stream(data)
+    info = st.info
+    pv, pl = lf_synth.random_requests(n, U * V, st.nloc, p["id"])
+    views = torch.from_numpy(pv.view(np.int32)).cuda()
+    locs = torch.from_numpy(pl.view(np.int32)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cur = torch.cuda.current_stream()
+    out_ref = torch.empty((n, 4, 4, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((n, 4, 4, 3), dtype=torch.uint8, device="cuda")
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            fn()
+            b.record(cur)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms)), float(np.mean(ms))
+
+    per_req_ms, _ = timed(lambda: st.decode_blocks(views, locs, out_ref), args.steps, args.warmup)
+    b = rlfc.Batch(st, n)
+    b.config = dict(graph=0)
+    chosen = b.autotune(views, locs, out)
+    eager_ms, _ = timed(lambda: b.decode(views, locs, out), args.steps, args.warmup)
+    identical_eager = bool(torch.equal(out, out_ref))
+    # per-kernel split of the eager path
+    rlfc.trace_read(reset=True)
+    rlfc.trace_enable(True)
+    eager_trace_steps = args.steps
+    for _ in range(eager_trace_steps):
+        flush.fill_(1)
+        b.decode(views, locs, out)
+    torch.cuda.synchronize()
+    trace = rlfc.trace_read(reset=True)
+    rlfc.trace_enable(False)
+    b.config = dict(graph=1)
+    out.zero_()
+    graph_ms, _ = timed(lambda: b.decode(views, locs, out), args.steps, args.warmup)
+    identical_graph = bool(torch.equal(out, out_ref))
+
+    # full decode of the light field, the bandwidth-bound form of the decoder
+    lf_out = torch.empty((U * V, p["H"], p["W"], 3), dtype=torch.uint8, device="cuda")
+    dec_ms, _ = timed(lambda: st.decode_all(lf_out), args.steps, args.warmup)
+
+    peak, peak_src = _peaks()
+    loc_words, nloc = _stream_location_words(data)
+    hit = np.unique(pl)
+    rec_bytes_hit = int(4 * loc_words[hit].sum())
+    # records of the locations hit, their offsets and top-RKV blocks, the
+    # requests read, 48 B written per request
+    alg_batch = rec_bytes_hit + 12 * len(hit) + 96 * info.n_top * len(hit) + 8 * n + 48 * n
+    stream_read = info.record_bytes + 4 * (3 * nloc + 1) + info.top_bytes
+    alg_dec = stream_read + U * V * p["W"] * p["H"] * 3
+    kern = {}
+    for name, (launches, tot) in trace.items():
+        kern[name] = {"launches": launches, "avg_ms": tot / max(launches, 1)}
+    dk = kern.get("decode_binned_kernel", {"avg_ms": eager_ms})
+    kbytes_binned = rec_bytes_hit + 12 * len(hit) + 96 * info.n_top * len(hit) + 4 * n + 8 * n + 48 * n
+    dk_gbs = kbytes_binned / (dk["avg_ms"] * 1e-3) / 1e9
+
+    # end to end: requests uploaded from pinned memory, blocks downloaded
+    h_v = torch.from_numpy(pv.view(np.int32)).pin_memory()
+    h_l = torch.from_numpy(pl.view(np.int32)).pin_memory()
+    h_out = torch.empty(out.shape, dtype=torch.uint8).pin_memory()
+    e_steps = min(args.steps, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(e_steps):
+        views.copy_(h_v, non_blocking=True)
+        locs.copy_(h_l, non_blocking=True)
+        b.decode(views, locs, out)
+        h_out.copy_(out, non_blocking=True)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1) / e_steps
+
+    # CPU oracle on a bounded sample of the requests
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ost = oracle.Stream(oracle.encode(lf, U, V, B=4, L=p["L"], c=p["c"], tau_p=tau, tau_b=16 * tau))
+        t_enc = time.perf_counter() - t0
+        k = min(n, args.cpu_sample_requests)
+        t0 = time.perf_counter()
+        for r in range(k):
+            ost.decode_block(int(pv[r]), int(pl[r]))
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": 16 * k / t_cpu / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle DecompressLFIBlock for the first {k} of the {n} requests "
+                         f"({t_cpu:.1f} s, 1 thread, one call each; stream written by the oracle "
+                         f"encoder in {t_enc:.0f} s)", "host_cpus": os.cpu_count()}
+
+    px = 16 * n
+    line = {"metric": METRIC, "value": px / (graph_ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"batching: {U}x{V} views of {p['W']}x{p['H']} RGB, 8 planes -3..3, "
+                                   f"contrast-modulated, 3-level tree {tuple(p['c'][1:])}, 4x4 blocks, tau {tau}; "
+                                   f"{n} uniform random (view, location) requests per launch",
+                       "U": U, "V": V, "W": p["W"], "H": p["H"], "levels": p["L"], "tau": tau,
+                       "n_requests": n, "stream_bytes": int(info.stream_bytes),
+                       "locations_hit": int(len(hit)), "nloc": int(nloc),
+                       "l2": "flushed by a 256 MiB write before every timed launch",
+                       "synth_s": t_synth},
+            "batched_graph": {"ms": graph_ms, "requests_per_s": n / (graph_ms * 1e-3),
+                              "config": chosen, "identical_to_per_request": identical_graph},
+            "batched_eager": {"ms": eager_ms, "requests_per_s": n / (eager_ms * 1e-3),
+                              "identical_to_per_request": identical_eager},
+            "per_request": {"ms": per_req_ms, "requests_per_s": n / (per_req_ms * 1e-3)},
+            "speedup_vs_per_request": per_req_ms / graph_ms,
+            "kernels": kern,
+            "roofline": {"bound": "hbm", "kernel": "decode_binned_kernel", "achieved": dk_gbs, "peak": peak,
+                         "unit": "GB/s", "frac": dk_gbs / peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                         "traffic": TRAFFIC_PER_LAUNCH.get(("batching", tau, n, "decode_binned_kernel")),
+                         "bytes_per_launch": kbytes_binned, "avg_launch_ms": dk["avg_ms"]},
+            "algorithmic_bytes_per_call": alg_batch,
+            "decode_all": {"ms": dec_ms, "mpix_s": U * V * p["W"] * p["H"] / (dec_ms * 1e-3) / 1e6,
+                           "algorithmic_bytes": alg_dec, "gbs": alg_dec / (dec_ms * 1e-3) / 1e9,
+                           "hbm_frac": alg_dec / (dec_ms * 1e-3) / 1e9 / peak},
+            "e2e": {"value": px / (e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+                    "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 48 * n, "steps": e_steps},
+            "cpu_baseline": cpu,
+            "gpu_launches": sum(v["launches"] for v in kern.values())}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,8 +575,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=400)
+    ap.add_argument("--workload", choices=["step", "batching"], default="step",
+                    help="step: decode-all + render (default); batching: random block requests")
+    ap.add_argument("--n-requests", type=int, default=None)
+    ap.add_argument("--cpu-sample-requests", type=int, default=200000)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "batching" and args.impl == "ours":
+        run_batching(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -160,6 +160,77 @@ RLFC_API int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const fl
                       uint32_t out_w, uint32_t out_h, size_t n, float *d_out,
                       void *cuda_stream);
 
+/*
+ * Batched random access (the paper's DecompressLFIBlock of Algorithm 2 for
+ * many requests at once, Section 3.5, which notes that blocks decode in
+ * parallel).  A batch object groups the requests of one call by block
+ * location (a counting sort on the GPU), then a persistent kernel takes
+ * locations from an atomic work queue: a warp parses a location's three
+ * channel records once (presence mask ranks, header lengths, payload offsets)
+ * and decodes the stored ancestor blocks of every request at that location,
+ * so the record gather is shared by all of them.  The results are the same
+ * bytes as rlfc_decode_blocks.
+ *
+ * Progressive decode (Section 3.6: stopping the traversal at a coarser
+ * level returns the filtered views): with level l > 0 a request returns the
+ * reconstruction of its view's level-l ancestor, i.e. the top RKV plus the
+ * residuals of levels L-2 down to l, converted to RGB and clamped;
+ * level L-1 returns the top RKV alone, level 0 the view itself.
+ */
+typedef struct rlfc_batch rlfc_batch;   /* opaque, library-owned */
+
+typedef struct {
+    uint32_t warps_per_cta;   /* 4, 8 or 16 */
+    uint32_t locs_per_pop;    /* locations a warp takes from the queue at once, 1..64 */
+    uint32_t stage;           /* 1: copy a location's records to shared memory before
+                                 parsing (when they fit); 0: read them through L1 */
+    uint32_t graph;           /* 1: replay the call as a captured CUDA graph */
+} rlfc_batch_config;
+
+/*
+ * Create a batch object for up to max_requests requests per call on stream s
+ * (which must outlive it).  It allocates its device scratch (about
+ * 8 B per request + 4 B per block location) on s's device, plus a private
+ * CUDA stream used only to capture graphs.  The default configuration is
+ * {8, 1, 0, 1}.  Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE (max_requests >=
+ * 2^31), RLFC_E_UNSUPPORTED (records too large for the decoder's shared
+ * memory), RLFC_E_OOM, RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_batch_create(const rlfc_stream *s, size_t max_requests, rlfc_batch **out);
+
+/* Set / read the configuration (validated; a new one drops the cached graph). */
+RLFC_API int rlfc_batch_set_config(rlfc_batch *b, const rlfc_batch_config *cfg);
+RLFC_API int rlfc_batch_get_config(const rlfc_batch *b, rlfc_batch_config *cfg);
+
+/*
+ * Decode n requests (view d_view[r], location d_loc[r], as for
+ * rlfc_decode_blocks) at tree level `level` (0 = the views, up to L-1) into
+ * d_out (n * 48 bytes, request-major, 16 RGB pixels row-major per block) and
+ * d_status (n bytes, may be NULL; a bad request gets a zeroed block).  With
+ * graph = 1 the first call with a given set of arguments captures the whole
+ * sequence (scratch clears, binning kernels, decode kernel) into a CUDA graph
+ * and later identical calls replay it.  Calls on one batch object share its
+ * scratch: serialise them (one object per CUDA stream).  n = 0 is a no-op.
+ * Errors: RLFC_E_INVALID_ARG (null pointer, level > L-1), RLFC_E_RANGE
+ * (n > max_requests), RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_batch_decode(rlfc_batch *b, const uint32_t *d_view, const uint32_t *d_loc, size_t n,
+                               uint32_t level, uint8_t *d_out, uint8_t *d_status, void *cuda_stream);
+
+/*
+ * Time every candidate configuration (warps per CTA 4/8/16, locations per
+ * pop 1/4, staging off/on) on these requests at level 0 with CUDA events,
+ * keep the fastest (the graph flag is left as it was) and write it to
+ * *chosen (may be NULL).  d_out and d_status receive the decoded requests.
+ * Synchronises `cuda_stream`.  Errors: as rlfc_batch_decode.
+ */
+RLFC_API int rlfc_batch_autotune(rlfc_batch *b, const uint32_t *d_view, const uint32_t *d_loc, size_t n,
+                                 uint8_t *d_out, uint8_t *d_status, void *cuda_stream,
+                                 rlfc_batch_config *chosen);
+
+/* Release a batch object (after its work finished). */
+RLFC_API void rlfc_batch_free(rlfc_batch *b);
+
 /* Encoder parameters (Algorithm 1, Section 3.1-3.3). */
 typedef struct {
     uint32_t U, V, W, H;  /* grid and view size */

@@ -20,6 +20,9 @@ to 17x17 views of 64^2 to 1024^2 pixels) and are seeded with
 """
 from __future__ import annotations
 
+import hashlib
+import os
+
 import numpy as np
 
 SEED_BASE = 1805_06019
@@ -139,9 +142,26 @@ def make_lightfield(U: int, V: int, W: int, H: int, disparities, sigma: float,
 
 
 def preset_lightfield(name: str) -> np.ndarray:
+    """The preset's views.  When RLFC_SYNTH_CACHE names a directory, the
+    views are kept there as .npy, keyed by preset and by this module's source,
+    so that several processes of one session synthesise a large preset once."""
     p = PRESETS[name]
-    return make_lightfield(p["U"], p["V"], p["W"], p["H"], p["disparities"], p["sigma"],
-                           p["id"], p.get("contrast", False))
+    cache = os.environ.get("RLFC_SYNTH_CACHE")
+    path = None
+    if cache:
+        with open(__file__, "rb") as f:
+            key = hashlib.sha1(f.read()).hexdigest()[:12]
+        path = os.path.join(cache, f"{name}_{key}.npy")
+        if os.path.exists(path):
+            return np.load(path)
+    lf = make_lightfield(p["U"], p["V"], p["W"], p["H"], p["disparities"], p["sigma"],
+                         p["id"], p.get("contrast", False))
+    if path:
+        os.makedirs(cache, exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp.npy"
+        np.save(tmp, lf)
+        os.replace(tmp, path)
+    return lf
 
 
 def random_views(n: int, U: int, V: int, preset_id: int, d_choices=(0.0,)) -> np.ndarray:

@@ -31,7 +31,7 @@ namespace rlfc {
 namespace {
 
 constexpr int kStrip = 16;       // block locations per CTA
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kLeafBatch = 16;
 constexpr int kRecs = 3 * kStrip;
@@ -60,7 +60,7 @@ struct Smem {
     int16_t *res;      // [kLeafBatch][48][kStrip]  leaf residuals
     uint8_t *rgb;      // [kWarps][row bytes]: one output row per warp
     uint32_t *mask;    // [kRecs][MW]
-    uint32_t *off;     // [kRecs][pmax]  payload bit offset of each stored block
+    void *off;         // [kRecs][pmax]  payload bit offset of each stored block (OffT)
     uint2 *list;       // [list_cap]  (node | record << 16, rank)
 };
 
@@ -68,6 +68,7 @@ extern __shared__ __align__(16) unsigned char g_smem[];
 
 __host__ __device__ inline size_t r16(size_t b) { return (b + 15) & ~size_t(15); }
 
+template <typename OffT>
 __device__ __forceinline__ Smem carve(const Args &a)
 {
     Smem m;
@@ -84,17 +85,18 @@ __device__ __forceinline__ Smem carve(const Args &a)
     p += r16((size_t)kWarps * kStrip * 16);
     m.mask = reinterpret_cast<uint32_t *>(p);
     p += r16(4ull * kRecs * a.MW);
-    m.off = reinterpret_cast<uint32_t *>(p);
-    p += r16(4ull * kRecs * a.pmax);
+    m.off = p;
+    p += r16(sizeof(OffT) * kRecs * a.pmax);
     m.list = reinterpret_cast<uint2 *>(p);
     return m;
 }
 
-inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap)
+inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap,
+                         size_t off_size)
 {
     return r16(4ull * S) + r16(2ull * n_top * 48 * kStrip) + r16(2ull * n_int * 48 * kStrip) +
            r16(2ull * kLeafBatch * 48 * kStrip) + r16((size_t)kWarps * kStrip * 16) +
-           r16(4ull * kRecs * MW) + r16(4ull * kRecs * pmax) + r16(8ull * list_cap);
+           r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap);
 }
 
 // Stored blocks of nodes [p0, p1) over the strip's records, compacted into the
@@ -139,9 +141,11 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
 // Decode the listed blocks, one block per thread; the residual
 // (min + u) * 2^(q + shift) goes to the node's slot in dst:
 // dst[((node - p0) * 48 + channel * 16 + value) * kStrip + location].
+template <typename OffT>
 __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
                                             uint32_t b0, uint32_t p0, int16_t *dst)
 {
+    const OffT *off = reinterpret_cast<const OffT *>(m.off);
     const uint32_t hdr0 = 32 * a.MW;
     for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         const uint2 it = m.list[i];
@@ -150,7 +154,7 @@ __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const 
         const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
         const BlockHeader h = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
         int32_t u[kVals];
-        bise_decode16(rec, m.off[r * a.pmax + rank], s_mode[h.mode], u);
+        bise_decode16(rec, off[r * a.pmax + rank], s_mode[h.mode], u);
         const int32_t scale = 1 << (a.q + h.shift);
         int16_t *d = dst + ((p - p0) * 48 + c * 16) * kStrip + loc;
 #pragma unroll
@@ -159,7 +163,7 @@ __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const 
     }
 }
 
-template <bool kPacked>
+template <bool kPacked, typename OffT>
 __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
 {
     constexpr uint32_t kRowBytes = kPacked ? kStrip * 16 : kStrip * 12;
@@ -169,7 +173,8 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
     const uint32_t bx0 = blockIdx.x * kStrip, by = blockIdx.y;
     const uint32_t nl = min((uint32_t)kStrip, a.nlx - bx0);
     const uint32_t b0 = by * a.nlx + bx0;
-    const Smem m = carve(a);
+    const Smem m = carve<OffT>(a);
+    OffT *m_off = reinterpret_cast<OffT *>(m.off);
 
     if (tid < kNumModes)
         s_mode[tid] = c_modes[tid];
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
             const uint32_t len = h < P ? mode_bits(s_mode[get_bits(rec, hdr0 + kHdrBits * h, 5)]) : 0u;
             const uint32_t incl = warp_inclusive_scan(len, lane);
             if (h < P)
-                m.off[r * a.pmax + h] = run + incl - len;
+                m_off[r * a.pmax + h] = (OffT)(run + incl - len);
             run += __shfl_sync(kFullMask, incl, 31);
         }
     }
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
     // ---- phase 2: internal nodes, decoded, then reconstructed level by level
     if (a.n_int > 0) {
         const uint32_t cnt = build_list(a, m, 0, a.n_int, &s_count, false);
-        decode_list(a, m, s_mode, cnt, b0, 0, m.inter);
+        decode_list<OffT>(a, m, s_mode, cnt, b0, 0, m.inter);
         __syncthreads();
         for (uint32_t p0 = 0; p0 < a.n_int;) {
             const uint32_t lvl = node_level(m.node[p0]);
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
         for (uint32_t i = tid; i < kLeafBatch * 48 * kStrip / 2; i += kThreads)
             reinterpret_cast<uint32_t *>(m.res)[i] = 0;
         const uint32_t cnt = build_list(a, m, p0, p0 + nb, &s_count, kPacked && a.needed != nullptr);
-        decode_list(a, m, s_mode, cnt, b0, p0, m.res);
+        decode_list<OffT>(a, m, s_mode, cnt, b0, p0, m.res);
         __syncthreads();
         // parent + residual -> RGB, one (leaf, pixel row) per warp step;
         // lane = (location, pixel pair)
@@ -333,17 +338,20 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.out_aligned16 = ((uintptr_t)d_out & 15u) == 0;
     a.pmax = std::max<uint32_t>(s->max_present, 1);
     a.list_cap = kRecs * std::max<uint32_t>(t.n_int, kLeafBatch);
-    const size_t smem = smem_bytes(a.S, a.n_top, a.n_int, a.MW, a.pmax, a.list_cap);
+    // payload offsets are bit positions inside one record: 16 bits suffice
+    // unless a record reaches 2^16 bits
+    const bool off16 = (uint64_t)s->max_record_words * 32 < 65536;
+    const size_t smem = smem_bytes(a.S, a.n_top, a.n_int, a.MW, a.pmax, a.list_cap, off16 ? 2 : 4);
     if (smem > kSmemBudget || a.S >= 65536) {
         set_error("tree too large for the decode-all kernel's shared memory");
         return RLFC_E_UNSUPPORTED;
     }
-    cudaError_t e = cudaFuncSetAttribute(decode_all_kernel<kPacked>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = off16 ? decode_all_kernel<kPacked, uint16_t> : decode_all_kernel<kPacked, uint32_t>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_all: shared memory attribute");
     dim3 grid((a.nlx + kStrip - 1) / kStrip, s->info.nloc_y);
-    { rlfc::TraceScope trace_((kPacked ? "decode_all_kernel<packed>" : "decode_all_kernel"), st); decode_all_kernel<kPacked><<<grid, kThreads, smem, st>>>(a); }
+    { rlfc::TraceScope trace_((kPacked ? "decode_all_kernel<packed>" : "decode_all_kernel"), st); kern<<<grid, kThreads, smem, st>>>(a); }
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_all launch");

@@ -241,22 +241,6 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
     return RLFC_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
-            cudaSetDevice(dev);
-        else
-            prev = -1;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0)
-            cudaSetDevice(prev);
-    }
-};
-
 void free_device(rlfc_stream *s)
 {
     cudaFree(s->d_records);

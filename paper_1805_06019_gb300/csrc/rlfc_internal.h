@@ -65,6 +65,24 @@ private:
     cudaStream_t st_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+
+// Makes `dev` current for its lifetime and restores the previous device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            cudaSetDevice(dev);
+        else
+            prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
 int build_tables(uint32_t L, const std::vector<uint32_t> &cnt,
                  const std::vector<std::vector<uint32_t>> &parent, Tables &t);
 int cuda_fail(cudaError_t e, const char *what);

@@ -38,13 +38,23 @@ class EncParams(ctypes.Structure):
                 ("q", ctypes.c_uint32)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_uint32), ("locs_per_pop", ctypes.c_uint32),
+                ("stage", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class TraceEntry(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char * 56), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
 
 EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
            "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_no_alloc",
-           "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read"]
+           "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read",
+           "rlfc_batch_create", "rlfc_batch_set_config", "rlfc_batch_get_config", "rlfc_batch_decode",
+           "rlfc_batch_autotune", "rlfc_batch_free"]
 
 _lib = None
 _lock = threading.Lock()
@@ -78,6 +88,13 @@ def lib():
             L.rlfc_strerror.restype = ctypes.c_char_p
             L.rlfc_last_error.argtypes = []
             L.rlfc_last_error.restype = ctypes.c_char_p
+            L.rlfc_batch_create.argtypes = [vp, sz, ctypes.POINTER(vp)]
+            L.rlfc_batch_set_config.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+            L.rlfc_batch_get_config.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+            L.rlfc_batch_decode.argtypes = [vp, vp, vp, sz, u32, vp, vp, vp]
+            L.rlfc_batch_autotune.argtypes = [vp, vp, vp, sz, vp, vp, vp, ctypes.POINTER(BatchConfig)]
+            L.rlfc_batch_free.argtypes = [vp]
+            L.rlfc_batch_free.restype = None
             L.rlfc_trace_enable.argtypes = [ctypes.c_int]
             L.rlfc_trace_read.argtypes = [ctypes.POINTER(TraceEntry), sz, ctypes.POINTER(sz), ctypes.c_int]
             _lib = L
@@ -194,6 +211,80 @@ class Stream:
             ctypes.c_void_p(_dev(disp, torch.float32, "disp")), out_w, out_h, n,
             ctypes.c_void_p(_dev(out, torch.float32, "out")), _stream_handle(stream)))
         return out
+
+
+def _u32_ptr(t: torch.Tensor, name: str) -> int:
+    return _dev(t, torch.int32, name) if t.dtype == torch.int32 else _dev(t, torch.uint32, name)
+
+
+class Batch:
+    """Batched random-access decode of one loaded stream (rlfc_batch_*):
+    requests grouped by location, one persistent kernel, optionally replayed
+    as a captured CUDA graph.  Calls on one object must not overlap."""
+
+    def __init__(self, stream: Stream, max_requests: int):
+        self.stream = stream          # keeps the stream alive
+        h = ctypes.c_void_p()
+        _check(lib().rlfc_batch_create(stream._h, int(max_requests), ctypes.byref(h)))
+        self._h = h
+        self.max_requests = int(max_requests)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rlfc_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(lib().rlfc_batch_get_config(self._h, ctypes.byref(c)))
+        return c.as_dict()
+
+    @config.setter
+    def config(self, cfg: dict):
+        c = BatchConfig()
+        cur = self.config
+        cur.update(cfg)
+        for k, v in cur.items():
+            setattr(c, k, int(v))
+        _check(lib().rlfc_batch_set_config(self._h, ctypes.byref(c)))
+
+    def decode(self, views: torch.Tensor, locs: torch.Tensor, out: torch.Tensor | None = None,
+               status: torch.Tensor | None = None, level: int = 0, stream=None):
+        """(out [n, 4, 4, 3] uint8, status [n] uint8 or None) at tree level
+        `level` (rlfc_batch_decode)."""
+        n = views.numel()
+        if locs.numel() != n:
+            raise ValueError("views and locs differ in length")
+        s = self.stream
+        if out is None:
+            out = torch.empty((n, s.B, s.B, 3), dtype=torch.uint8, device="cuda")
+        if n == 0:
+            return out, status
+        st_ptr = ctypes.c_void_p(_dev(status, torch.uint8, "status")) if status is not None else None
+        _check(lib().rlfc_batch_decode(self._h, ctypes.c_void_p(_u32_ptr(views, "views")),
+                                       ctypes.c_void_p(_u32_ptr(locs, "locs")), n, int(level),
+                                       ctypes.c_void_p(_dev(out, torch.uint8, "out")), st_ptr,
+                                       _stream_handle(stream)))
+        return out, status
+
+    def autotune(self, views: torch.Tensor, locs: torch.Tensor, out: torch.Tensor,
+                 status: torch.Tensor | None = None, stream=None) -> dict:
+        """Time the candidate configurations on these requests and keep the
+        fastest (rlfc_batch_autotune); returns it."""
+        c = BatchConfig()
+        st_ptr = ctypes.c_void_p(_dev(status, torch.uint8, "status")) if status is not None else None
+        _check(lib().rlfc_batch_autotune(self._h, ctypes.c_void_p(_u32_ptr(views, "views")),
+                                         ctypes.c_void_p(_u32_ptr(locs, "locs")), views.numel(),
+                                         ctypes.c_void_p(_dev(out, torch.uint8, "out")), st_ptr,
+                                         _stream_handle(stream), ctypes.byref(c)))
+        return c.as_dict()
 
 
 def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: int = 0,
