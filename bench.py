@@ -563,6 +563,90 @@ def run_batching(args):
     print(json.dumps(line))
 
 
+def run_serving(args):
+    """Eight resident light fields (three 5x5x256^2, three 9x9x512^2, two
+    17x17x1024^2), view requests at their native sizes arriving as a Poisson
+    process at several rates, served with continuous batching; latency is
+    submit -> view copied to pinned host memory."""
+    import torch
+    from paper_1805_06019_gb300 import rlfc
+
+    torch.cuda.set_device(0)
+    streams, grids = [], []
+    t0 = time.time()
+    for name, tau in lf_synth.SERVING_FLEET:
+        p = lf_synth.PRESETS[name]
+        lf = lf_synth.preset_lightfield(name)
+        d_lf = torch.from_numpy(lf).cuda()
+        data = rlfc.encode(d_lf, p["U"], p["V"], p["L"], p["c"], tau_p=tau, tau_b=16 * tau)
+        del d_lf, lf
+        streams.append(rlfc.Stream(data))
+        grids.append((p["U"], p["V"], p["W"], p["H"], p["disparities"]))
+    t_setup = time.time() - t0
+    resident = sum(int(s.info.device_bytes) for s in streams)
+    budget = args.serve_budget << 20
+    srv = rlfc.Server(n_streams=args.serve_streams, max_batch=args.serve_max_batch, memory_budget=budget,
+                      max_inflight=args.serve_inflight)
+    ids = [srv.add(s) for s in streams]
+    # pinned destinations, reused once their request has completed
+    pool = {}
+    for U, V, W, H, _ in grids:
+        if (W, H) not in pool:
+            pool[(W, H)] = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+                            for _ in range(args.serve_pool)]
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    results = []
+    for ri, rate in enumerate(rates):
+        n = max(int(rate * args.serve_seconds), 50)
+        arr = lf_synth.poisson_arrivals(rate, n, preset_id=4 + ri)
+        lf_i, fu, fv, fd = lf_synth.serving_requests(n, len(streams), preset_id=4 + ri)
+        free = {k: list(range(len(v))) for k, v in pool.items()}
+        owner = {}
+        comps, waited = [], 0
+        base = rlfc.Server.now() + 0.05
+        for i in range(n):
+            U, V, W, H, disp = grids[lf_i[i]]
+            while not free[(W, H)]:
+                waited += 1
+                for c in srv.poll():
+                    comps.append(c)
+                    free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
+            slot = free[(W, H)].pop()
+            while rlfc.Server.now() < base + arr[i]:
+                pass
+            t = srv.submit(ids[lf_i[i]], fu[i] * (U - 1), fv[i] * (V - 1),
+                           disp[min(int(fd[i] * len(disp)), len(disp) - 1)], pool[(W, H)][slot])
+            owner[t] = ((W, H), slot)
+            if i % 16 == 0:
+                for c in srv.poll():
+                    comps.append(c)
+                    free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
+        comps += srv.poll(wait=True)
+        lat = np.array([c["t_done"] - c["t_submit"] for c in comps]) * 1e3
+        span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
+        px = sum(grids[c["lf"]][2] * grids[c["lf"]][3] for c in comps)
+        results.append({"rate_req_s": rate, "requests": n, "ok": int(sum(c["status"] == 0 for c in comps)),
+                        "views_per_s": len(comps) / span, "mpix_s": px / span / 1e6,
+                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                        "mean_batch": float(np.mean([c["batch"] for c in comps])),
+                        "client_waits_for_buffers": waited})
+    srv.close()
+    top = results[-1]
+    line = {"metric": METRIC, "value": top["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: 8 resident light fields (3x 5x5x256^2 tau 2/4/8, 3x 9x9x512^2 "
+                                   "tau 2/4/8, 2x 17x17x1024^2 tau 4/8), native-size view requests, "
+                                   "Poisson arrivals; latency = submit to view in pinned host memory",
+                       "rates": rates, "seconds_per_rate": args.serve_seconds,
+                       "n_streams": args.serve_streams, "max_batch": args.serve_max_batch,
+                       "max_inflight": args.serve_inflight,
+                       "memory_budget_mib": args.serve_budget, "resident_device_bytes": resident,
+                       "setup_s": t_setup},
+            "serving": results}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,13 +659,23 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=400)
-    ap.add_argument("--workload", choices=["step", "batching"], default="step",
-                    help="step: decode-all + render (default); batching: random block requests")
+    ap.add_argument("--workload", choices=["step", "batching", "serving"], default="step",
+                    help="step: decode-all + render (default); batching: random block requests; "
+                         "serving: Poisson view requests on resident light fields")
+    ap.add_argument("--serve-rates", default="500,1000,2000,5000")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-max-batch", type=int, default=64)
+    ap.add_argument("--serve-budget", type=int, default=2048, help="MiB of outputs in flight")
+    ap.add_argument("--serve-inflight", type=int, default=1, help="render calls queued per stream")
+    ap.add_argument("--serve-pool", type=int, default=48, help="pinned destinations per view size")
     ap.add_argument("--n-requests", type=int, default=None)
     ap.add_argument("--cpu-sample-requests", type=int, default=200000)
     args = ap.parse_args()
     if args.workload == "batching" and args.impl == "ours":
         run_batching(args)
+    elif args.workload == "serving" and args.impl == "ours":
+        run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -231,6 +231,78 @@ RLFC_API int rlfc_batch_autotune(rlfc_batch *b, const uint32_t *d_view, const ui
 /* Release a batch object (after its work finished). */
 RLFC_API void rlfc_batch_free(rlfc_batch *b);
 
+/*
+ * Serving (the interactive use the paper targets, Sections 1 and 5: new
+ * views of resident compressed light fields on demand; the paper has no
+ * serving runtime of its own).  A server keeps loaded streams on the device
+ * and runs one worker thread that batches view requests continuously:
+ *  - rlfc_server_submit queues a request (light field, camera (u, v), focus
+ *    disparity, output size, host destination) and returns at once;
+ *  - the worker admits queued requests in arrival order while the device
+ *    memory of their outputs fits the memory budget, groups the admitted ones
+ *    by (light field, output size) into calls of rlfc_render_views of at most
+ *    max_batch views, and issues each call on the least busy of n_streams
+ *    CUDA streams that holds fewer than max_inflight calls, followed by the
+ *    copy of every view to its host destination;
+ *  - requests that arrive while earlier calls run are admitted as soon as
+ *    memory frees, and their calls overlap the earlier ones on other streams;
+ *  - a completed request (its copy to the host done) is reported by
+ *    rlfc_server_poll with its submit, start and completion times (seconds on
+ *    the clock of rlfc_server_now).
+ * A view's pixels do not depend on which other requests shared its call, so
+ * every result equals that of rendering the request alone.
+ */
+typedef struct rlfc_server rlfc_server;   /* opaque, library-owned */
+
+typedef struct {
+    uint32_t n_streams;       /* CUDA streams calls are spread over, 1..64 */
+    uint32_t max_batch;       /* views per render call, 1..4096 */
+    uint64_t memory_budget;   /* device bytes of outputs in flight (out_w*out_h*12 + 12 per view) */
+    uint32_t max_inflight;    /* calls queued on one stream at a time, 1..64: while every stream
+                                 is full, arrivals wait and then share the next call */
+    uint32_t pad;
+} rlfc_server_config;
+
+typedef struct {
+    uint64_t ticket;          /* from rlfc_server_submit */
+    int32_t status;           /* RLFC_OK or the render call's error code */
+    uint32_t lf;              /* light-field id */
+    uint32_t batch;           /* views in the call that served it */
+    uint32_t pad;
+    double t_submit, t_start, t_done;   /* rlfc_server_now() clock, seconds */
+} rlfc_completion;
+
+/* Start a server on the current CUDA device.  Errors: RLFC_E_INVALID_ARG,
+ * RLFC_E_OOM, RLFC_E_CUDA. */
+RLFC_API int rlfc_server_create(const rlfc_server_config *cfg, rlfc_server **out);
+
+/* Make a loaded stream servable (it must be on the server's device and
+ * outlive the server); *lf_id receives its id.  Errors: RLFC_E_INVALID_ARG. */
+RLFC_API int rlfc_server_add(rlfc_server *srv, const rlfc_stream *s, uint32_t *lf_id);
+
+/*
+ * Queue one view request; host_out (out_h * out_w * 3 floats, ideally pinned)
+ * receives the view and must stay valid until the request completes.
+ * Thread-safe.  Errors: RLFC_E_INVALID_ARG (unknown id, null pointer, empty
+ * size), RLFC_E_RANGE (one view larger than the memory budget or than
+ * rlfc_render_views accepts).
+ */
+RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
+                                uint32_t out_w, uint32_t out_h, float *host_out, uint64_t *ticket);
+
+/*
+ * Move up to `cap` completed requests into out (oldest first) and set *n.
+ * With wait != 0 the call first blocks until every submitted request has
+ * completed.  Errors: RLFC_E_INVALID_ARG.
+ */
+RLFC_API int rlfc_server_poll(rlfc_server *srv, rlfc_completion *out, size_t cap, size_t *n, int wait);
+
+/* Seconds on the server's monotonic clock. */
+RLFC_API double rlfc_server_now(void);
+
+/* Finish the queued requests, stop the worker and release the server. */
+RLFC_API void rlfc_server_free(rlfc_server *srv);
+
 /* Encoder parameters (Algorithm 1, Section 3.1-3.3). */
 typedef struct {
     uint32_t U, V, W, H;  /* grid and view size */

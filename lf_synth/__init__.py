@@ -179,3 +179,28 @@ def random_requests(n: int, n_views: int, n_loc: int, preset_id: int):
     views = rng.integers(0, n_views, size=n, dtype=np.uint32)
     locs = rng.integers(0, n_loc, size=n, dtype=np.uint32)
     return views, locs
+
+
+def poisson_arrivals(rate: float, n: int, preset_id: int, stream: int = 4) -> np.ndarray:
+    """n arrival times (seconds from 0) of a Poisson process of `rate`
+    requests per second: cumulative sums of exponential gaps."""
+    rng = rng_for(preset_id, stream)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+SERVING_FLEET = [
+    # (preset, residual threshold): three 5x5x256^2, three 9x9x512^2 and two
+    # 17x17x1024^2 light fields, each size class encoded at different
+    # thresholds so that every resident stream differs
+    ("serving_small", 2), ("serving_small", 4), ("serving_small", 8),
+    ("serving_medium", 2), ("serving_medium", 4), ("serving_medium", 8),
+    ("serving_large", 4), ("serving_large", 8),
+]
+
+
+def serving_requests(n: int, n_lf: int, preset_id: int, stream: int = 5):
+    """n requests as (light-field index, u01, v01, plane choice u01): uniform
+    over the resident light fields, camera position and focus plane drawn as
+    fractions that the caller maps to each light field's grid and planes."""
+    rng = rng_for(preset_id, stream)
+    return (rng.integers(0, n_lf, size=n), rng.random(n), rng.random(n), rng.random(n))

@@ -46,6 +46,17 @@ class BatchConfig(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("memory_budget", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("lf", ctypes.c_uint32),
+                ("batch", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class TraceEntry(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char * 56), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -54,7 +65,8 @@ EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_dec
            "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_no_alloc",
            "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read",
            "rlfc_batch_create", "rlfc_batch_set_config", "rlfc_batch_get_config", "rlfc_batch_decode",
-           "rlfc_batch_autotune", "rlfc_batch_free"]
+           "rlfc_batch_autotune", "rlfc_batch_free", "rlfc_server_create", "rlfc_server_add",
+           "rlfc_server_submit", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free"]
 
 _lib = None
 _lock = threading.Lock()
@@ -95,6 +107,15 @@ def lib():
             L.rlfc_batch_autotune.argtypes = [vp, vp, vp, sz, vp, vp, vp, ctypes.POINTER(BatchConfig)]
             L.rlfc_batch_free.argtypes = [vp]
             L.rlfc_batch_free.restype = None
+            L.rlfc_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+            L.rlfc_server_add.argtypes = [vp, vp, ctypes.POINTER(u32)]
+            L.rlfc_server_submit.argtypes = [vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float, u32, u32, vp,
+                                             ctypes.POINTER(ctypes.c_uint64)]
+            L.rlfc_server_poll.argtypes = [vp, ctypes.POINTER(Completion), sz, ctypes.POINTER(sz), ctypes.c_int]
+            L.rlfc_server_now.argtypes = []
+            L.rlfc_server_now.restype = ctypes.c_double
+            L.rlfc_server_free.argtypes = [vp]
+            L.rlfc_server_free.restype = None
             L.rlfc_trace_enable.argtypes = [ctypes.c_int]
             L.rlfc_trace_read.argtypes = [ctypes.POINTER(TraceEntry), sz, ctypes.POINTER(sz), ctypes.c_int]
             _lib = L
@@ -285,6 +306,72 @@ class Batch:
                                          ctypes.c_void_p(_dev(out, torch.uint8, "out")), st_ptr,
                                          _stream_handle(stream), ctypes.byref(c)))
         return c.as_dict()
+
+
+class Server:
+    """Serving runtime (rlfc_server_*): resident streams, a worker thread that
+    batches view requests continuously over several CUDA streams, admission
+    by device memory.  Results land in host tensors given at submit."""
+
+    def __init__(self, n_streams: int = 4, max_batch: int = 64, memory_budget: int = 1 << 30,
+                 max_inflight: int = 1):
+        cfg = ServerConfig(n_streams, max_batch, memory_budget, max_inflight, 0)
+        h = ctypes.c_void_p()
+        _check(lib().rlfc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._streams = []
+        self._outs = {}
+
+    def add(self, stream: Stream) -> int:
+        lf = ctypes.c_uint32()
+        _check(lib().rlfc_server_add(self._h, stream._h, ctypes.byref(lf)))
+        self._streams.append(stream)
+        return lf.value
+
+    def submit(self, lf: int, u: float, v: float, disp: float, out: torch.Tensor) -> int:
+        """Queue a view of out.shape [H, W, 3] (float32 host tensor, ideally
+        pinned); returns its ticket."""
+        if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.dim() != 3:
+            raise TypeError("out must be a contiguous float32 host tensor [H, W, 3]")
+        t = ctypes.c_uint64()
+        _check(lib().rlfc_server_submit(self._h, int(lf), float(u), float(v), float(disp), out.shape[1],
+                                        out.shape[0], ctypes.c_void_p(out.data_ptr()), ctypes.byref(t)))
+        self._outs[t.value] = out          # keep the destination alive until completion
+        return t.value
+
+    def poll(self, wait: bool = False, cap: int = 4096) -> list:
+        """Completed requests as dicts (ticket, status, lf, batch, t_submit,
+        t_start, t_done); wait=True first waits for every submitted one."""
+        arr = (Completion * cap)()
+        n = ctypes.c_size_t()
+        res = []
+        first = True
+        while True:
+            _check(lib().rlfc_server_poll(self._h, arr, cap, ctypes.byref(n), 1 if (wait and first) else 0))
+            first = False
+            for k in range(n.value):
+                c = arr[k]
+                res.append({"ticket": int(c.ticket), "status": int(c.status), "lf": int(c.lf),
+                            "batch": int(c.batch), "t_submit": c.t_submit, "t_start": c.t_start,
+                            "t_done": c.t_done})
+                self._outs.pop(int(c.ticket), None)
+            if n.value < cap:
+                return res
+
+    @staticmethod
+    def now() -> float:
+        return lib().rlfc_server_now()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rlfc_server_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: int = 0,
