@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SRCS = ["colour.c", "bise.c", "tree.c", "encode.c", "decode.c", "render.c"]
+_SRCS = ["colour.c", "bise.c", "tree.c", "encode.c", "decode.c", "render.c", "ks.c", "mlp.c"]
 _MAXL = 8
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +61,8 @@ class _Params(ctypes.Structure):
         ("U", ctypes.c_int), ("V", ctypes.c_int), ("W", ctypes.c_int), ("H", ctypes.c_int),
         ("B", ctypes.c_int), ("L", ctypes.c_int), ("c", ctypes.c_int * _MAXL),
         ("tau_p", ctypes.c_int), ("tau_b", ctypes.c_int), ("q", ctypes.c_int),
+        ("mode_space", ctypes.c_int), ("tau_err", ctypes.c_int), ("lam_q8", ctypes.c_int),
+        ("leaf_modes", ctypes.c_void_p), ("leaf_resid", ctypes.c_void_p), ("leaf_label", ctypes.c_void_p),
     ]
 
 
@@ -119,6 +121,13 @@ def lib():
             d = ctypes.c_double
             L.or_render_pixel.argtypes = [v, i, i, i, i, d, d, d, i, i, i, i, v]
             L.or_render_view.argtypes = [v, i, i, i, i, d, d, d, i, i, v]
+            L.or_ks_quantise.argtypes = [v, i, i, i, v]
+            L.or_ks_cost.argtypes = [v, i, i, i, i, i, i, _P(ctypes.c_longlong)]
+            L.or_ks_search.argtypes = [v, i, i, i, i, _P(i), _P(i)]
+            L.or_ks_features.argtypes = [v, v]
+            L.or_mlp_nparams.argtypes = []
+            L.or_mlp_forward.argtypes = [v, v, i, v]
+            L.or_mlp_loss_grad.argtypes = [v, v, v, i, v, _P(d)]
         return _lib
 
 
@@ -230,10 +239,16 @@ def filter_level(child: np.ndarray, Gu: int, Gv: int, c: int) -> np.ndarray:
 # ---- Algorithm 1: encoder ----------------------------------------------------
 
 def encode(lf: np.ndarray, U: int, V: int, B: int = 4, L: int = 2, c=(0, 5),
-           tau_p: int = 0, tau_b: int = 0, q: int = 0) -> bytes:
+           tau_p: int = 0, tau_b: int = 0, q: int = 0, mode_space: int = 0, tau_err: int = 0,
+           lam_q8: int = 0, leaf_modes: np.ndarray | None = None, leaf_out: dict | None = None) -> bytes:
     """Compress views lf[V*U, H, W, 3] (uint8) into an RLFC stream (format v1).
 
     c[l] is the cluster side used to build level l from level l-1 (c[0] unused).
+    mode_space 1 picks each block's (mode, shift) with ks_search (tau_err,
+    lam_q8), or takes the level-0 ones from leaf_modes [U*V, 3, nloc] uint8
+    (k | s << 5, 0xFF = search).  leaf_out, when given, receives "resid"
+    [U*V, 3, nloc, B*B] int16 and "label" [U*V, 3, nloc] uint8 of the level-0
+    blocks.
     """
     a = np.ascontiguousarray(lf, dtype=np.uint8)
     H, W = a.shape[-3], a.shape[-2]
@@ -243,6 +258,19 @@ def encode(lf: np.ndarray, U: int, V: int, B: int = 4, L: int = 2, c=(0, 5),
     for l in range(1, L):
         p.c[l] = int(c[l])
     p.tau_p, p.tau_b, p.q = int(tau_p), int(tau_b), int(q)
+    p.mode_space, p.tau_err, p.lam_q8 = int(mode_space), int(tau_err), int(lam_q8)
+    nloc = ((W + B - 1) // B) * ((H + B - 1) // B)
+    keep = []
+    if leaf_modes is not None:
+        lm = np.ascontiguousarray(leaf_modes, dtype=np.uint8)
+        assert lm.size == U * V * 3 * nloc
+        keep.append(lm)
+        p.leaf_modes = lm.ctypes.data
+    if leaf_out is not None:
+        leaf_out["resid"] = np.zeros((U * V, 3, nloc, B * B), dtype=np.int16)
+        leaf_out["label"] = np.zeros((U * V, 3, nloc), dtype=np.uint8)
+        p.leaf_resid = leaf_out["resid"].ctypes.data
+        p.leaf_label = leaf_out["label"].ctypes.data
     out = ctypes.POINTER(ctypes.c_uint8)()
     n = ctypes.c_size_t()
     rc = lib().or_encode(_ptr(a), ctypes.byref(p), ctypes.byref(out), ctypes.byref(n))
@@ -353,3 +381,70 @@ def psnr_ycocg(orig: np.ndarray, dec: np.ndarray, cap: float = 99.0) -> float:
 def bpp(stream: bytes, n_pixels: int) -> float:
     """Bits per (24-bit RGB) pixel of the whole stream."""
     return 8.0 * len(stream) / n_pixels
+
+
+# ---- the learned encoder aid: (mode, shift) search, statistics, network ------
+
+NCLASSES = 4 * NMODES   # class s * 28 + k
+
+
+def ks_search(r, q: int = 0, tau_err: int = 0, lam_q8: int = 0):
+    """(k, s) of the exhaustive search over the 112 (shift, mode) pairs for
+    the residual block r (16 ints), or None when no pair fits."""
+    a = np.ascontiguousarray(r, dtype=np.int32)
+    k, s_ = ctypes.c_int(), ctypes.c_int()
+    if lib().or_ks_search(_ptr(a), a.size, q, tau_err, lam_q8, ctypes.byref(k), ctypes.byref(s_)) != 0:
+        return None
+    return k.value, s_.value
+
+
+def ks_cost(r, q: int, s: int, k: int, tau_err: int, lam_q8: int):
+    """256 * bits + lam_q8 * SSE of (s, k) for block r, or None when (s, k)
+    is not a candidate."""
+    a = np.ascontiguousarray(r, dtype=np.int32)
+    c = ctypes.c_longlong()
+    if lib().or_ks_cost(_ptr(a), a.size, q, s, k, tau_err, lam_q8, ctypes.byref(c)) != 0:
+        return None
+    return c.value
+
+
+def ks_quantise(r, q: int, s: int) -> np.ndarray:
+    a = np.ascontiguousarray(r, dtype=np.int32)
+    out = np.empty_like(a)
+    lib().or_ks_quantise(_ptr(a), a.size, q, s, _ptr(out))
+    return out
+
+
+def ks_features(r) -> np.ndarray:
+    """The 48 block statistics (float64) of a 16-value residual block."""
+    a = np.ascontiguousarray(r, dtype=np.int32)
+    assert a.size == 16
+    f = np.empty(48, dtype=np.float64)
+    lib().or_ks_features(_ptr(a), _ptr(f))
+    return f
+
+
+def mlp_nparams() -> int:
+    return lib().or_mlp_nparams()
+
+
+def mlp_forward(w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Logits [n, 112] (float64) of the aid's network for inputs x [n, 48]."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    out = np.empty((n, NCLASSES), dtype=np.float64)
+    lib().or_mlp_forward(_ptr(w), _ptr(x), n, _ptr(out))
+    return out
+
+
+def mlp_loss_grad(w: np.ndarray, x: np.ndarray, y: np.ndarray):
+    """(summed cross-entropy, summed gradient [P]) in float64."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    g = np.empty(mlp_nparams(), dtype=np.float64)
+    loss = ctypes.c_double()
+    if lib().or_mlp_loss_grad(_ptr(w), _ptr(x), _ptr(y), x.shape[0], _ptr(g), ctypes.byref(loss)) != 0:
+        raise ValueError("label out of range")
+    return loss.value, g

@@ -25,7 +25,10 @@
  *    (round half away from zero), reconstructed as qv * 2^q.  A kept block
  *    whose quantised values are all zero is dropped as well.
  *  - BISE range per block: min = min(qv) goes in the block header, the values
- *    qv - min are coded with the cheapest mode that holds their span.
+ *    qv - min are coded with the cheapest mode that holds their span.  With
+ *    mode_space 1 each block instead gets the (mode, shift) of or_ks_search
+ *    (ks.c), or a given one for the level-0 blocks, and is quantised with
+ *    the global shift plus its own shift s (header bits 5..6).
  *  - Images whose side is not a multiple of B are padded by repeating the last
  *    column / row.
  *
@@ -128,7 +131,8 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
     *out = NULL;
     *nbytes = 0;
     if (p->U < 1 || p->V < 1 || p->W < 1 || p->H < 1 || p->B < 1 || p->B > 8 ||
-        p->L < 2 || p->L > OR_MAXL || p->tau_p < 0 || p->tau_b < 0 || p->q < 0 || p->q > 7)
+        p->L < 2 || p->L > OR_MAXL || p->tau_p < 0 || p->tau_b < 0 || p->q < 0 || p->q > 7 ||
+        p->mode_space < 0 || p->mode_space > 1 || p->tau_err < 0 || p->lam_q8 < 0)
         return -1;
     const int U = p->U, V = p->V, W = p->W, H = p->H, B = p->B, L = p->L, q = p->q;
     const int n = B * B;
@@ -175,6 +179,8 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
        of a node replaces its RKV image in img[] once used; present[] marks the
        kept blocks.  rec[l] is the recomputed level l (rec[L-1] = top RKVs). */
     unsigned char *present[OR_MAXL] = {0};
+    unsigned char *kmode[OR_MAXL] = {0};   /* per stored block: k | s << 5 */
+    int srv_err = 0;
     rec[L - 1] = malloc(sizeof(int32_t) * npix * nodes[L - 1]);
     memcpy(rec[L - 1], img[L - 1], sizeof(int32_t) * npix * nodes[L - 1]);
     const int half = q > 0 ? 1 << (q - 1) : 0;
@@ -183,6 +189,7 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
     for (int l = L - 1; l >= 1; l--) {
         int lc = l - 1;
         present[lc] = calloc((size_t)nodes[lc] * 3 * nloc, 1);
+        kmode[lc] = calloc((size_t)nodes[lc] * 3 * nloc, 1);
         if (lc >= 1)
             rec[lc] = malloc(sizeof(int32_t) * npix * nodes[lc]);
         for (int x = 0; x < nodes[lc]; x++) {
@@ -200,20 +207,57 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
                         energy += resid < 0 ? -resid : resid;
                     }
                     int keep = energy > 0 && energy >= p->tau_b;
+                    const long bi = ((long)x * 3 + c) * nloc + b;
+                    int ks_k = 0, ks_s = 0, have = 0;
+                    if (lc == 0 && p->leaf_resid)
+                        for (int k = 0; k < n; k++)
+                            p->leaf_resid[bi * n + k] = (int16_t)r[k];
+                    if (lc == 0 && p->leaf_label) {
+                        int lk, ls;
+                        p->leaf_label[bi] = keep && or_ks_search(r, n, q, p->tau_err, p->lam_q8, &lk, &ls) == 0
+                                                ? (uint8_t)(lk | ls << 5) : 0xFF;
+                    }
+                    if (keep && p->mode_space == 1) {
+                        /* a given leaf mode is used when it is a candidate */
+                        if (lc == 0 && p->leaf_modes && p->leaf_modes[bi] != 0xFF) {
+                            long long cost;
+                            int gk = p->leaf_modes[bi] & 31, gs = p->leaf_modes[bi] >> 5;
+                            if (or_ks_cost(r, n, q, gs, gk, p->tau_err, p->lam_q8, &cost) == 0) {
+                                ks_k = gk;
+                                ks_s = gs;
+                                have = 1;
+                            }
+                        }
+                        if (!have && or_ks_search(r, n, q, p->tau_err, p->lam_q8, &ks_k, &ks_s) != 0)
+                            srv_err = 1;
+                    }
+                    const int t = q + ks_s;
+                    const int ht = t > 0 ? 1 << (t - 1) : 0;
                     int nonzero = 0;
                     for (int k = 0; k < n; k++) {
                         int mag = r[k] < 0 ? -r[k] : r[k];
-                        int qm = (mag + half) >> q;
+                        int qm = (mag + (p->mode_space == 1 ? ht : half)) >> (p->mode_space == 1 ? t : q);
                         qv[k] = keep ? (r[k] < 0 ? -qm : qm) : 0;
                         if (qv[k] != 0)
                             nonzero = 1;
                     }
                     if (!nonzero)
                         keep = 0;
-                    present[lc][((long)x * 3 + c) * nloc + b] = (unsigned char)keep;
+                    if (keep && p->mode_space == 0) {
+                        int mn = qv[0], mx = qv[0];
+                        for (int k = 1; k < n; k++) {
+                            if (qv[k] < mn) mn = qv[k];
+                            if (qv[k] > mx) mx = qv[k];
+                        }
+                        ks_k = or_choose_mode_search(n, mx - mn);
+                        if (ks_k < 0)
+                            srv_err = 1;
+                    }
+                    present[lc][bi] = (unsigned char)keep;
+                    kmode[lc][bi] = (unsigned char)(keep ? (ks_k | ks_s << 5) : 0);
                     for (int k = 0; k < n; k++) {
                         long at = c * plane + (long)(by * B + k / B) * Wp + bx * B + k % B;
-                        int add = keep ? qv[k] * (1 << q) : 0;
+                        int add = keep ? qv[k] * (1 << (q + ks_s)) : 0;
                         if (lc >= 1)
                             rec[lc][(long)x * npix + at] = rec[l][(long)par * npix + at] + add;
                         img[lc][(long)x * npix + at] = keep ? qv[k] : 0;
@@ -237,7 +281,7 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
     /* pass 1: the length of every record */
     long *rec_words = malloc(sizeof(long) * 3 * nloc);
     int *u = malloc(sizeof(int) * n);
-    int err = 0;
+    int err = srv_err;
     long total_words = 0;
     for (int b = 0; b < nloc && !err; b++) {
         int bx = b % nlx, by = b / nlx;
@@ -254,8 +298,8 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
                     if (k == 0 || v < mn) mn = v;
                     if (k == 0 || v > mx) mx = v;
                 }
-                int mode = or_choose_mode_search(n, mx - mn);
-                if (mode < 0 || mn < -1024 || mn > 1023) {
+                int mode = kmode[lv][((long)nd * 3 + c) * nloc + b] & 31;
+                if (or_mode_N(mode) < mx - mn + 1 || mn < -1024 || mn > 1023) {
                     err = 1;
                     break;
                 }
@@ -337,8 +381,9 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
                     }
                     for (int k = 0; k < n; k++)
                         u[k] -= mn;
-                    int mode = or_choose_mode_search(n, mx - mn);
-                    uint32_t header = (uint32_t)mode | (0u << 5) | (((uint32_t)mn & 0x7FFu) << 7);
+                    const int km = kmode[lv][((long)nd * 3 + c) * nloc + b];
+                    int mode = km & 31;
+                    uint32_t header = (uint32_t)mode | ((uint32_t)(km >> 5) << 5) | (((uint32_t)mn & 0x7FFu) << 7);
                     or_put_bits(recp, hdr_pos, HDR_BITS, header);
                     hdr_pos += HDR_BITS;
                     or_bise_pack(recp, pay_pos, n, mode, u);
@@ -359,6 +404,7 @@ int or_encode(const uint8_t *rgb, const or_params *p, uint8_t **out, size_t *nby
         free(img[l]);
         free(rec[l]);
         free(present[l]);
+        free(kmode[l]);
     }
     or_tree_free(&tree);
     return buf ? 0 : -1;

@@ -80,6 +80,18 @@ typedef struct {
     int tau_p;             /* pixel threshold: |r| < tau_p -> 0 */
     int tau_b;             /* block energy threshold: sum|r| < tau_b -> dropped */
     int q;                 /* global quantisation shift */
+    /* block modes: 0 = plain method (s = 0, cheapest range); 1 = per-block
+       (mode, shift) by or_ks_search, or taken from leaf_modes when given */
+    int mode_space;
+    int tau_err;           /* largest error a shift s > 0 may add */
+    int lam_q8;            /* distortion weight of the search, 1/256 bits per squared error */
+    const uint8_t *leaf_modes;  /* optional [U*V][3][nloc]: k | s << 5 for the level-0
+                                   blocks, 0xFF = search; an infeasible entry falls back
+                                   to the search (mode_space 1 only) */
+    int16_t *leaf_resid;   /* optional out [U*V][3][nloc][n]: level-0 residuals after the
+                              pixel threshold */
+    uint8_t *leaf_label;   /* optional out [U*V][3][nloc]: or_ks_search's k | s << 5 for the
+                              level-0 blocks kept by the energy test, 0xFF for the others */
 } or_params;
 
 /* rgb: [V][U][H][W][3].  On success *out is malloc'ed; release with or_free. */
@@ -88,6 +100,19 @@ void or_free(void *ptr);
 /* binomial cluster filter of one level (Eq. 2), exposed for tests */
 int or_filter_level(const int32_t *child, int Gu, int Gv, int c, int npix,
                     int32_t *parent_out);
+
+/* ---- ks.c : per-block (mode, shift) search of the learned encoder aid ---- */
+void or_ks_quantise(const int *r, int n, int q, int s, int *qv);
+/* 0 and *cost = 256 * bits + lam_q8 * SSE when (s, k) is a candidate, else -1 */
+int or_ks_cost(const int *r, int n, int q, int s, int k, int tau_err, int lam_q8, long long *cost);
+int or_ks_search(const int *r, int n, int q, int tau_err, int lam_q8, int *k_out, int *s_out);
+/* the 48 statistics of a 16-value block, in the network's input order */
+void or_ks_features(const int *r, double *f);
+
+/* ---- mlp.c : the aid's network, 48 -> 64 -> 64 -> 112, FP64 ---- */
+int or_mlp_nparams(void);
+void or_mlp_forward(const double *w, const double *x, int n, double *logits);
+int or_mlp_loss_grad(const double *w, const double *x, const int *y, int n, double *grad, double *loss);
 
 /* ---- decode.c : Algorithm 2 ---- */
 typedef struct {
