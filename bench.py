@@ -647,6 +647,92 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_learned(args):
+    """The learned encoder aid on the 15 x 15 x 625 x 434 light field
+    (lenslet-like disparities within +-1, sigma 2, 3-level (3, 5) tree):
+    level-0 blocks labelled by the exhaustive (shift, mode) search, the
+    network trained on the GPU, mode agreement on held-out blocks, and bpp /
+    PSNR of the plain, searched and aided encodes."""
+    import torch
+    from paper_1805_06019_gb300 import learned, rlfc
+
+    torch.cuda.set_device(0)
+    p = lf_synth.PRESETS["learned"]
+    U, V, W, H, L, c = p["U"], p["V"], p["W"], p["H"], p["L"], p["c"]
+    tau = args.tau if args.tau is not None else p["taus"][0]
+    lam = args.lam_q8
+    lf = lf_synth.preset_lightfield("learned")
+    d = torch.from_numpy(lf).cuda()
+    px = U * V * W * H
+    cur = torch.cuda.current_stream()
+
+    def ev_time(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        r = fn()
+        b.record(cur)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    plain = rlfc.encode(d, U, V, L, c, tau_p=tau, tau_b=16 * tau)
+    searched, resid, label, index, n = learned.leaf_dataset(d, U, V, L, c, tau, 16 * tau, 0, tau, lam)
+    x, y = learned.features(resid, label, index, n)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(0)
+    perm = torch.randperm(n, generator=g).cuda()
+    n_train = int(0.9 * n)
+    tr, te = perm[:n_train], perm[n_train:]
+    aid = learned.Aid(seed=0)
+    t0 = time.time()
+    hist = aid.train(x[tr], y[tr], epochs=args.epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    pred_te = aid.predict(x[te])
+    agree = float((pred_te == y[te]).float().mean().item())
+    classes = torch.bincount(y[tr].long(), minlength=256)
+    majority = float(classes.max().item()) / n_train
+    pred_all = aid.predict(x)
+    agree_all = float((pred_all == y).float().mean().item())
+    aided = learned.encode_aided(d, U, V, L, c, tau, 16 * tau, aid, x, index, resid.shape[0], 0, tau, lam)
+    # per-block decision time: exhaustive search vs statistics + network
+    blocks = resid.index_select(0, index.long())
+    for _ in range(3):
+        learned.search(blocks, 0, tau, lam)
+        xs, _ = learned.features(blocks, None, None, n)
+        aid.predict(xs)
+    _, t_search = ev_time(lambda: learned.search(blocks, 0, tau, lam))
+    _, t_feat = ev_time(lambda: learned.features(blocks, None, None, n))
+    _, t_pred = ev_time(lambda: aid.predict(xs))
+
+    def quality(data):
+        dec = rlfc.Stream(data).decode_all().cpu().numpy()
+        return {"bytes": len(data), "bpp": 8.0 * len(data) / px, "psnr_db": learned.psnr_ycocg(lf, dec)}
+
+    q_plain, q_search, q_aided = quality(plain), quality(searched), quality(aided)
+    hist_labels = torch.bincount(y.long(), minlength=256).cpu().numpy()
+    shift_share = [float(hist_labels[(s_ << 5):(s_ << 5) + 28].sum()) / n for s_ in range(4)]
+    line = {"metric": METRIC, "value": agree, "unit": "mode agreement (held-out blocks)", "n_gpus": 1,
+            "steps": args.epochs, "warmup": 0, "ms_per_step": train_s * 1e3 / max(args.epochs, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": f"learned encoder aid: {U}x{V} views of {W}x{H} RGB, disparities within "
+                                   f"+-1, sigma 2, 3-level tree {tuple(c[1:])}, tau {tau}; level-0 blocks kept "
+                                   f"by the energy test labelled by the exhaustive (shift, mode) search "
+                                   f"(tau_err {tau}, lambda {lam}/256); 90/10 split",
+                       "labelled_blocks": n, "train_blocks": n_train, "epochs": args.epochs, "batch": 4096},
+            "train_loss_per_epoch": hist, "train_s": train_s,
+            "agreement_heldout": agree, "agreement_all": agree_all, "majority_class_share": majority,
+            "label_shift_share": shift_share,
+            "plain": q_plain, "search": q_search, "aided": q_aided,
+            "aided_vs_plain": {"bpp_change": q_aided["bpp"] - q_plain["bpp"],
+                               "psnr_change_db": q_aided["psnr_db"] - q_plain["psnr_db"]},
+            "aided_vs_search": {"bpp_change": q_aided["bpp"] - q_search["bpp"],
+                                "psnr_change_db": q_aided["psnr_db"] - q_search["psnr_db"]},
+            "decision_ns_per_block": {"search": t_search * 1e6 / n, "statistics": t_feat * 1e6 / n,
+                                      "network": t_pred * 1e6 / n}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,7 +745,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-views", type=int, default=400)
-    ap.add_argument("--workload", choices=["step", "batching", "serving"], default="step",
+    ap.add_argument("--workload", choices=["step", "batching", "serving", "learned"], default="step",
                     help="step: decode-all + render (default); batching: random block requests; "
                          "serving: Poisson view requests on resident light fields")
     ap.add_argument("--serve-rates", default="500,1000,2000,5000")
@@ -670,12 +756,16 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=1, help="render calls queued per stream")
     ap.add_argument("--serve-pool", type=int, default=48, help="pinned destinations per view size")
     ap.add_argument("--n-requests", type=int, default=None)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--lam-q8", type=int, default=256, help="distortion weight of the mode search, /256")
     ap.add_argument("--cpu-sample-requests", type=int, default=200000)
     args = ap.parse_args()
     if args.workload == "batching" and args.impl == "ours":
         run_batching(args)
     elif args.workload == "serving" and args.impl == "ours":
         run_serving(args)
+    elif args.workload == "learned" and args.impl == "ours":
+        run_learned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

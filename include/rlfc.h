@@ -312,6 +312,16 @@ typedef struct {
     int32_t tau_p;        /* pixel threshold: |r| < tau_p is zeroed */
     int32_t tau_b;        /* block energy threshold: sum |r| < tau_b drops the block */
     uint32_t q;           /* global quantisation shift, 0..7 */
+    /* block modes: 0 = the plain method (shift 0, the smallest range that holds
+       the span); 1 = per block the (shift s, mode k) of least cost
+       256 * payload bits + lam_q8 * SSE among the pairs whose range holds the
+       span of qv = sign(r) floor((|r| + 2^(q+s-1)) / 2^(q+s)) and, for s > 0,
+       whose error |r - qv 2^(q+s)| stays within tau_err (the header's shift
+       field, reconstructed as qv 2^(q+s)); this mode space is the learned
+       encoder aid's and has no counterpart in the paper */
+    uint32_t mode_space;
+    int32_t tau_err;
+    uint32_t lam_q8;
 } rlfc_enc_params;
 
 /*
@@ -340,6 +350,22 @@ typedef struct {
  */
 RLFC_API int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream,
                 void **host_out, size_t *nbytes);
+
+/*
+ * rlfc_encode with the learned encoder aid's hooks for the level-0 (view)
+ * blocks, whose index is (view * 3 + channel) * nloc + location:
+ *  - d_leaf_modes (device, may be NULL; mode_space 1 only): a given k | s << 5
+ *    per block, used when it is a candidate (see rlfc_enc_params), otherwise
+ *    and for 0xFF the search decides;
+ *  - d_leaf_resid (device, may be NULL): receives each block's 16 residuals
+ *    after the pixel threshold, int16;
+ *  - d_leaf_label (device, may be NULL): receives the search's k | s << 5 for
+ *    the blocks the energy test keeps, 0xFF for the others.
+ * Errors: as rlfc_encode.
+ */
+RLFC_API int rlfc_encode_ex(const rlfc_enc_params *p, const uint8_t *d_rgb, const uint8_t *d_leaf_modes,
+                            int16_t *d_leaf_resid, uint8_t *d_leaf_label, void *cuda_stream,
+                            void **host_out, size_t *nbytes);
 
 /*
  * The same encoder for callers that cannot allocate device memory while they
@@ -391,6 +417,63 @@ typedef struct {
 
 RLFC_API int rlfc_trace_enable(int on);
 RLFC_API int rlfc_trace_read(rlfc_trace_entry *out, size_t cap, size_t *n, int reset);
+
+/*
+ * Learned encoder aid (no counterpart in the paper; it sits beside the encoder
+ * and never changes how a stream decodes).  A small network predicts each
+ * level-0 block's (shift, mode) from 48 statistics of its residuals; the
+ * exhaustive search stays the judge and the fallback (rlfc_encode_ex takes a
+ * predicted mode only when it is a candidate).  All pointers are device
+ * pointers; every call is asynchronous on `cuda_stream`.
+ *
+ * Network: 48 -> 64 (ReLU) -> 64 (ReLU) -> 112 logits, class s * 28 + k.
+ * Parameters (RLFC_MLP_PARAMS, flat, in this order): W1 [64][48], b1 [64],
+ * W2 [64][64], b2 [64], W3 [112][64], b3 [112] (rows are output units), stored
+ * as BF16 (uint16 bit patterns); products and sums are FP32.
+ * Labels are header bytes k | s << 5.
+ */
+#define RLFC_KS_FEATURES 48
+#define RLFC_KS_CLASSES 112
+#define RLFC_MLP_PARAMS 14576
+
+/* The search of rlfc_enc_params for n blocks of 16 int16 residuals:
+ * d_label[i] = k | s << 5, or 0xFF when no pair is a candidate.
+ * Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE (n >= 2^31), RLFC_E_CUDA. */
+RLFC_API int rlfc_ks_search(const int16_t *d_resid, size_t n, uint32_t q, int32_t tau_err, uint32_t lam_q8,
+                            uint8_t *d_label, void *cuda_stream);
+
+/* Positions of the entries of d_label[0..n) that are not 0xFF, ascending,
+ * into d_index; their number into *d_count (device).  Errors: as above. */
+RLFC_API int rlfc_ks_compact(const uint8_t *d_label, size_t n, uint32_t *d_index, uint32_t *d_count,
+                             void *cuda_stream);
+
+/* The 48 statistics (BF16) of blocks d_resid[d_index[i]] (or [i] when
+ * d_index is NULL) into d_x [n][48]: the values sorted ascending / 32, the
+ * values in raster order / 32, mean, standard deviation, min, max / 32,
+ * span / 64, max |r| / 32, sum |r| / 256, the counts of non-zero, odd,
+ * 2 (mod 4), 4 (mod 8), |r| <= 1, 2, 4, 8 values / 16, log2(span + 1) / 10.
+ * d_label_out (may be NULL) receives d_label[d_index[i]].  Errors: as above. */
+RLFC_API int rlfc_ks_features(const int16_t *d_resid, const uint8_t *d_label, const uint32_t *d_index, size_t n,
+                              uint16_t *d_x, uint8_t *d_label_out, void *cuda_stream);
+
+/* Training step, forward and backward: for the samples d_order[0..n) (or
+ * 0..n) of (d_x, d_label), add the summed softmax cross-entropy to *d_loss
+ * and its summed gradient to d_grad [RLFC_MLP_PARAMS] (FP32; sums over CTAs
+ * use atomics, so the last bits vary between runs).  Labels whose mode is not
+ * below 28 are skipped.  Errors: as above. */
+RLFC_API int rlfc_mlp_loss_grad(const uint16_t *d_w, const uint16_t *d_x, const uint8_t *d_label,
+                                const uint32_t *d_order, size_t n, float *d_grad, float *d_loss, void *cuda_stream);
+
+/* Adam update of the FP32 master parameters from grad * grad_scale (step =
+ * 1, 2, ... for the bias corrections), refreshing the BF16 copy d_w and
+ * clearing d_grad.  Errors: RLFC_E_INVALID_ARG, RLFC_E_CUDA. */
+RLFC_API int rlfc_mlp_adam(float *d_master, uint16_t *d_w, float *d_grad, float *d_m, float *d_v, float lr,
+                           float beta1, float beta2, float eps, float grad_scale, uint32_t step, void *cuda_stream);
+
+/* Inference: the predicted label (first largest logit) of each sample i goes
+ * to d_label[d_index[i]] (or [i]).  Errors: as rlfc_ks_search. */
+RLFC_API int rlfc_mlp_predict(const uint16_t *d_w, const uint16_t *d_x, size_t n, const uint32_t *d_index,
+                              uint8_t *d_label, void *cuda_stream);
 
 /* Free a host buffer returned by the library. */
 RLFC_API void rlfc_free_host(void *p);

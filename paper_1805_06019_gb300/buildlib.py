@@ -10,8 +10,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librlfc.so")
 SOURCES = ["rlfc_host.cu", "trace.cu", "decode_batch.cu", "server.cu", "decode_all.cu", "decode_blocks.cu", "render.cu", "render_native.cu",
-           "encode.cu", "encode_no_alloc.cu"]
-HEADERS = ["rlfc_device.cuh", "rlfc_internal.h", "warp_decode.cuh"]
+           "encode.cu", "encode_no_alloc.cu", "mlp.cu"]
+HEADERS = ["rlfc_device.cuh", "rlfc_internal.h", "warp_decode.cuh", "ks_device.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -26,6 +26,8 @@ __constant__ uint32_t c_rangeN[kNumModes] = {1,  2,  3,  4,   5,   6,   8,   10,
                                              48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024};
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
 
+#include "ks_device.cuh"
+
 __global__ void ycocg_pad_kernel(const uint8_t *rgb, int16_t *x0, uint32_t n_views, uint32_t W, uint32_t H,
                                  uint32_t Wp, uint32_t Hp)
 {
@@ -73,10 +75,19 @@ struct SrvArgs {
     int16_t *rec_child;       // reconstruction of level l-1 (null for level 0)
     const uint32_t *parent;   // parent index of each child node
     uint8_t *present;         // [child node][3][nloc]
+    uint8_t *kmode;           // [child node][3][nloc]: k | s << 5 of a stored block
+    const uint8_t *leaf_modes;   // level 0 only, may be null: given k | s << 5, 0xFF = search
+    int16_t *leaf_resid;      // level 0 only, may be null: residuals after the pixel threshold
+    uint8_t *leaf_label;      // level 0 only, may be null: search result, 0xFF = not kept
+    int *error;
     uint32_t n_child, nlx, nloc, Wp, Hp;
     int32_t tau_p, tau_b;
     uint32_t q;
+    uint32_t mode_space, lam_q8;
+    int32_t tau_err;
 };
+
+// (shift, mode) search: ks_device.cuh, included above with these tables in scope
 
 // Eq. 3 with the thresholds and quantisation of Section 3.2, one thread per
 // (child node, channel, block location).
@@ -104,23 +115,60 @@ __global__ void srv_kernel(const SrvArgs a)
             energy += abs(v);
         }
         bool keep = energy > 0 && energy >= a.tau_b;
-        const int half = a.q > 0 ? 1 << (a.q - 1) : 0;
+        const size_t bi = ((size_t)node * 3 + c) * a.nloc + loc;
+        if (a.leaf_resid) {
+#pragma unroll
+            for (int k = 0; k < kVals; k++)
+                a.leaf_resid[bi * kVals + k] = (int16_t)r[k];
+        }
+        if (a.leaf_label) {
+            uint32_t lk = 0, ls = 0;
+            a.leaf_label[bi] = keep && ks_search(r, a.q, a.tau_err, a.lam_q8, lk, ls) ? (uint8_t)(lk | ls << 5)
+                                                                                     : (uint8_t)0xFF;
+        }
+        uint32_t ks_k = 0, ks_s = 0;
+        if (keep && a.mode_space) {
+            bool have = false;
+            if (a.leaf_modes && a.leaf_modes[bi] != 0xFF) {
+                // a given mode is used when it is a candidate
+                const uint32_t gk = a.leaf_modes[bi] & 31u, gs = a.leaf_modes[bi] >> 5;
+                long long cost;
+                if (ks_cost(r, a.q, gs, gk, a.tau_err, a.lam_q8, cost)) {
+                    ks_k = gk;
+                    ks_s = gs;
+                    have = true;
+                }
+            }
+            if (!have && !ks_search(r, a.q, a.tau_err, a.lam_q8, ks_k, ks_s))
+                atomicExch(a.error, 3);
+        }
+        const uint32_t t = a.q + ks_s;
+        const int half = t > 0 ? 1 << (t - 1) : 0;
         bool nonzero = false;
+        int mn = 0, mx = 0;
 #pragma unroll
         for (int k = 0; k < kVals; k++) {
-            const int qm = (abs(r[k]) + half) >> a.q;
+            const int qm = (abs(r[k]) + half) >> t;
             r[k] = keep ? (r[k] < 0 ? -qm : qm) : 0;
             nonzero |= r[k] != 0;
+            mn = k == 0 ? r[k] : min(mn, r[k]);
+            mx = k == 0 ? r[k] : max(mx, r[k]);
         }
         keep = keep && nonzero;
-        a.present[((size_t)node * 3 + c) * a.nloc + loc] = keep ? 1 : 0;
+        if (keep && !a.mode_space) {
+            // the plain method: the smallest range that holds the span
+            while (ks_k < kNumModes - 1 && (int)c_rangeN[ks_k] < mx - mn + 1)
+                ks_k++;
+        }
+        a.present[bi] = keep ? 1 : 0;
+        a.kmode[bi] = keep ? (uint8_t)(ks_k | ks_s << 5) : 0;
         int16_t *rc = a.rec_child ? a.rec_child + ((size_t)node * 3 + c) * plane : nullptr;
 #pragma unroll
         for (int k = 0; k < kVals; k++) {
             const size_t at = (size_t)(by * 4 + k / 4) * a.Wp + bx * 4 + k % 4;
             const int qv = keep ? r[k] : 0;
             if (rc)
-                rc[at] = (int16_t)(xp[at] + qv * (1 << a.q));
+                rc[at] = (int16_t)(xp[at] + qv * (1 << t));
             xc[at] = (int16_t)qv;
         }
     }
@@ -129,6 +177,7 @@ __global__ void srv_kernel(const SrvArgs a)
 struct RecArgs {
     const int16_t *const *srv;   // per level < L-1: quantised SRV images
     const uint8_t *const *present;
+    const uint8_t *const *kmode;  // per level < L-1: k | s << 5 of each stored block
     const uint32_t *bfs_level;   // [S]
     const uint32_t *bfs_node;    // [S]
     uint32_t S, MW, nlx, nloc, Wp, Hp;
@@ -138,28 +187,19 @@ struct RecArgs {
 };
 
 __device__ __forceinline__ void load_block(const RecArgs &a, uint32_t pos, uint32_t c, uint32_t loc,
-                                           int v[kVals], bool &present)
+                                           int v[kVals], bool &present, uint32_t &km)
 {
     const uint32_t lv = a.bfs_level[pos], nd = a.bfs_node[pos];
     present = a.present[lv][((size_t)nd * 3 + c) * a.nloc + loc] != 0;
     if (!present)
         return;
+    km = a.kmode[lv][((size_t)nd * 3 + c) * a.nloc + loc];
     const size_t plane = (size_t)a.Wp * a.Hp;
     const int16_t *img = a.srv[lv] + ((size_t)nd * 3 + c) * plane;
     const uint32_t bx = loc % a.nlx, by = loc / a.nlx;
 #pragma unroll
     for (int k = 0; k < kVals; k++)
         v[k] = img[(size_t)(by * 4 + k / 4) * a.Wp + bx * 4 + k % 4];
-}
-
-// smallest range that holds span + 1 values (the cheapest mode, since the
-// payload length grows with the range)
-__device__ __forceinline__ uint32_t pick_mode(int span)
-{
-    uint32_t k = 0;
-    while (k < kNumModes - 1 && c_rangeN[k] < (uint32_t)span + 1)
-        k++;
-    return k;
 }
 
 __global__ void record_size_kernel(const RecArgs a)
@@ -172,7 +212,8 @@ __global__ void record_size_kernel(const RecArgs a)
     for (uint32_t pos = 0; pos < a.S; pos++) {
         int v[kVals];
         bool present;
-        load_block(a, pos, c, loc, v, present);
+        uint32_t km = 0;
+        load_block(a, pos, c, loc, v, present, km);
         if (!present)
             continue;
         int mn = v[0], mx = v[0];
@@ -181,9 +222,9 @@ __global__ void record_size_kernel(const RecArgs a)
             mn = min(mn, v[k]);
             mx = max(mx, v[k]);
         }
-        if (mx - mn > 1023 || mn < -1024 || mn > 1023)
+        if ((int)c_rangeN[km & 31u] < mx - mn + 1 || mn < -1024 || mn > 1023)
             atomicExch(a.error, 1);
-        bits += kHdrBits + mode_bits(c_modes[pick_mode(mx - mn)]);
+        bits += kHdrBits + mode_bits(c_modes[km & 31u]);
     }
     a.words[r] = (bits + 31) / 32;
 }
@@ -235,31 +276,29 @@ __global__ void record_pack_kernel(const RecArgs a)
     for (uint32_t pos = 0; pos < a.S; pos++) {
         int v[kVals];
         bool present;
-        load_block(a, pos, c, loc, v, present);
+        uint32_t km = 0;
+        load_block(a, pos, c, loc, v, present, km);
         if (!present)
             continue;
-        int mn = v[0], mx = v[0];
+        int mn = v[0];
 #pragma unroll
-        for (int k = 1; k < kVals; k++) {
+        for (int k = 1; k < kVals; k++)
             mn = min(mn, v[k]);
-            mx = max(mx, v[k]);
-        }
-        bw.put(pick_mode(mx - mn) | (((uint32_t)mn & 0x7FFu) << 7), kHdrBits);
+        bw.put((km & 31u) | ((km >> 5) << 5) | (((uint32_t)mn & 0x7FFu) << 7), kHdrBits);
     }
     // payloads: digit words, then the low bits
     for (uint32_t pos = 0; pos < a.S; pos++) {
         int v[kVals];
         bool present;
-        load_block(a, pos, c, loc, v, present);
+        uint32_t km = 0;
+        load_block(a, pos, c, loc, v, present, km);
         if (!present)
             continue;
-        int mn = v[0], mx = v[0];
+        int mn = v[0];
 #pragma unroll
-        for (int k = 1; k < kVals; k++) {
+        for (int k = 1; k < kVals; k++)
             mn = min(mn, v[k]);
-            mx = max(mx, v[k]);
-        }
-        const uint32_t m = c_modes[pick_mode(mx - mn)];
+        const uint32_t m = c_modes[km & 31u];
         const uint32_t b = mode_b(m), kind = mode_kind(m);
         uint32_t u[kVals];
 #pragma unroll
@@ -377,7 +416,11 @@ size_t encode_scratch_bound(const rlfc_enc_params *p)
             add(2 * npix * cnt[l]);
         if (l + 1 < L)
             add(cnt[l] * 3 * nloc);
+        if (l + 1 < L)
+            add(cnt[l] * 3 * nloc);
     }
+    add(sizeof(int));
+    add(sizeof(void *) * L);
     for (uint32_t l = 1; l < L; l++) {
         add(4 * (cnt[l] + 1));
         add(4 * cnt[l - 1]);
@@ -398,14 +441,16 @@ size_t encode_scratch_bound(const rlfc_enc_params *p)
 }
 
 int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, std::vector<uint8_t> &out,
-               uint8_t *arena, size_t arena_size)
+               uint8_t *arena, size_t arena_size, const uint8_t *d_leaf_modes, int16_t *d_leaf_resid,
+               uint8_t *d_leaf_label)
 {
     if (p->B != 4) {
         set_error("the GPU encoder writes 4x4 blocks only");
         return RLFC_E_UNSUPPORTED;
     }
     if (p->U < 1 || p->V < 1 || (uint64_t)p->U * p->V > 16383 || p->W < 1 || p->H < 1 || p->W > 65536 ||
-        p->H > 65536 || p->L < 2 || p->L > (uint32_t)kMaxLevels || p->tau_p < 0 || p->tau_b < 0 || p->q > 7) {
+        p->H > 65536 || p->L < 2 || p->L > (uint32_t)kMaxLevels || p->tau_p < 0 || p->tau_b < 0 || p->q > 7 ||
+        p->mode_space > 1 || p->tau_err < 0) {
         set_error("encoder parameters out of range");
         return RLFC_E_INVALID_ARG;
     }
@@ -453,7 +498,7 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     buf.arena_size = arena_size;
     cudaError_t e;
     std::vector<int16_t *> img(L, nullptr), rec(L, nullptr);
-    std::vector<uint8_t *> present(L, nullptr);
+    std::vector<uint8_t *> present(L, nullptr), kmode(L, nullptr);
     for (uint32_t l = 0; l < L; l++) {
         if ((e = buf.alloc(&img[l], npix * cnt[l])) != cudaSuccess)
             return cuda_fail(e, "encoder allocation");
@@ -461,7 +506,13 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
             return cuda_fail(e, "encoder allocation");
         if (l + 1 < L && (e = buf.alloc(&present[l], (size_t)cnt[l] * 3 * nloc)) != cudaSuccess)
             return cuda_fail(e, "encoder allocation");
+        if (l + 1 < L && (e = buf.alloc(&kmode[l], (size_t)cnt[l] * 3 * nloc)) != cudaSuccess)
+            return cuda_fail(e, "encoder allocation");
     }
+    int *d_err;
+    if ((e = buf.alloc(&d_err, 1)) != cudaSuccess)
+        return cuda_fail(e, "encoder allocation");
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
     rec[L - 1] = img[L - 1];
     const int threads = 256;
     auto grid_for = [](size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 64); };
@@ -524,6 +575,14 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
         s.rec_child = (l - 1 >= 1) ? rec[l - 1] : nullptr;
         s.parent = d_par;
         s.present = present[l - 1];
+        s.kmode = kmode[l - 1];
+        s.leaf_modes = l == 1 ? d_leaf_modes : nullptr;
+        s.leaf_resid = l == 1 ? d_leaf_resid : nullptr;
+        s.leaf_label = l == 1 ? d_leaf_label : nullptr;
+        s.error = d_err;
+        s.mode_space = p->mode_space;
+        s.lam_q8 = p->lam_q8;
+        s.tau_err = p->tau_err;
         s.n_child = cnt[l - 1];
         s.nlx = nlx;
         s.nloc = nloc;
@@ -551,24 +610,24 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     }
     const uint32_t S = tab.S, MW = (S + 31) / 32;
     uint32_t *d_bl, *d_bn, *d_words_n, *d_off, *d_rec;
-    int *d_err;
     const int16_t **d_srv;
-    const uint8_t **d_pres;
+    const uint8_t **d_pres, **d_km;
     if ((e = buf.alloc(&d_bl, S)) != cudaSuccess || (e = buf.alloc(&d_bn, S)) != cudaSuccess ||
         (e = buf.alloc(&d_words_n, 3ull * nloc)) != cudaSuccess || (e = buf.alloc(&d_off, 3ull * nloc + 1)) != cudaSuccess ||
-        (e = buf.alloc(&d_err, 1)) != cudaSuccess || (e = buf.alloc(&d_srv, L)) != cudaSuccess ||
-        (e = buf.alloc(&d_pres, L)) != cudaSuccess)
+        (e = buf.alloc(&d_srv, L)) != cudaSuccess || (e = buf.alloc(&d_pres, L)) != cudaSuccess ||
+        (e = buf.alloc(&d_km, L)) != cudaSuccess)
         return cuda_fail(e, "encoder allocation");
     std::vector<const int16_t *> srv_ptrs(img.begin(), img.end());
-    std::vector<const uint8_t *> pres_ptrs(present.begin(), present.end());
+    std::vector<const uint8_t *> pres_ptrs(present.begin(), present.end()), km_ptrs(kmode.begin(), kmode.end());
     cudaMemcpyAsync(d_bl, bfs_level.data(), 4ull * S, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_bn, bfs_node.data(), 4ull * S, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_srv, srv_ptrs.data(), sizeof(void *) * L, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_pres, pres_ptrs.data(), sizeof(void *) * L, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    cudaMemcpyAsync(d_km, km_ptrs.data(), sizeof(void *) * L, cudaMemcpyHostToDevice, st);
     RecArgs ra;
     ra.srv = d_srv;
     ra.present = d_pres;
+    ra.kmode = d_km;
     ra.bfs_level = d_bl;
     ra.bfs_node = d_bn;
     ra.S = S;
@@ -588,7 +647,8 @@ int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st, 
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "encoder record sizes");
     if (h_err) {
-        set_error("a residual block's range does not fit the 28 BISE modes");
+        set_error(h_err == 3 ? "a residual block has no (mode, shift) candidate"
+                             : "a residual block's range does not fit the 28 BISE modes");
         return RLFC_E_RANGE;
     }
     uint64_t total = 0;

@@ -424,6 +424,13 @@ int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_di
 int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream, void **host_out,
                 size_t *nbytes)
 {
+    return rlfc_encode_ex(p, d_rgb, nullptr, nullptr, nullptr, cuda_stream, host_out, nbytes);
+}
+
+int rlfc_encode_ex(const rlfc_enc_params *p, const uint8_t *d_rgb, const uint8_t *d_leaf_modes,
+                   int16_t *d_leaf_resid, uint8_t *d_leaf_label, void *cuda_stream, void **host_out,
+                   size_t *nbytes)
+{
     if (!p || !d_rgb || !host_out || !nbytes) {
         set_error("null argument");
         return RLFC_E_INVALID_ARG;
@@ -432,7 +439,8 @@ int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_strea
     *nbytes = 0;
     try {
         std::vector<uint8_t> out;
-        int rc = encode_gpu(p, d_rgb, (cudaStream_t)cuda_stream, out);
+        int rc = encode_gpu(p, d_rgb, (cudaStream_t)cuda_stream, out, nullptr, 0, d_leaf_modes, d_leaf_resid,
+                            d_leaf_label);
         if (rc != RLFC_OK)
             return rc;
         void *buf = std::malloc(out.size());

@@ -98,8 +98,12 @@ int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, 
                   uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st);
 // arena: when given, every device buffer of the encoder is carved from it
 // (arena_size bytes) instead of being allocated
+// d_leaf_modes / d_leaf_resid / d_leaf_label: optional level-0 mode input and
+// training-data outputs (see rlfc_encode_ex)
 int encode_gpu(const rlfc_enc_params *p, const uint8_t *d_rgb, cudaStream_t st,
-               std::vector<uint8_t> &out, uint8_t *arena = nullptr, size_t arena_size = 0);
+               std::vector<uint8_t> &out, uint8_t *arena = nullptr, size_t arena_size = 0,
+               const uint8_t *d_leaf_modes = nullptr, int16_t *d_leaf_resid = nullptr,
+               uint8_t *d_leaf_label = nullptr);
 size_t encode_scratch_bound(const rlfc_enc_params *p);
 
 }  // namespace rlfc

@@ -35,7 +35,8 @@ class EncParams(ctypes.Structure):
     _fields_ = [("U", ctypes.c_uint32), ("V", ctypes.c_uint32), ("W", ctypes.c_uint32),
                 ("H", ctypes.c_uint32), ("B", ctypes.c_uint32), ("L", ctypes.c_uint32),
                 ("c", ctypes.c_uint32 * 8), ("tau_p", ctypes.c_int32), ("tau_b", ctypes.c_int32),
-                ("q", ctypes.c_uint32)]
+                ("q", ctypes.c_uint32), ("mode_space", ctypes.c_uint32), ("tau_err", ctypes.c_int32),
+                ("lam_q8", ctypes.c_uint32)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -62,11 +63,13 @@ class TraceEntry(ctypes.Structure):
 
 
 EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
-           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_no_alloc",
+           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_ex", "rlfc_encode_no_alloc",
            "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read",
            "rlfc_batch_create", "rlfc_batch_set_config", "rlfc_batch_get_config", "rlfc_batch_decode",
            "rlfc_batch_autotune", "rlfc_batch_free", "rlfc_server_create", "rlfc_server_add",
-           "rlfc_server_submit", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free"]
+           "rlfc_server_submit", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free",
+           "rlfc_ks_search", "rlfc_ks_compact", "rlfc_ks_features", "rlfc_mlp_loss_grad", "rlfc_mlp_adam",
+           "rlfc_mlp_predict"]
 
 _lib = None
 _lock = threading.Lock()
@@ -93,6 +96,8 @@ def lib():
             L.rlfc_decode_blocks.argtypes = [vp, vp, vp, sz, vp, vp, vp]
             L.rlfc_render_views.argtypes = [vp, vp, vp, u32, u32, sz, vp, vp]
             L.rlfc_encode.argtypes = [ctypes.POINTER(EncParams), vp, vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
+            L.rlfc_encode_ex.argtypes = [ctypes.POINTER(EncParams), vp, vp, vp, vp, vp, ctypes.POINTER(vp),
+                                         ctypes.POINTER(sz)]
             L.rlfc_encode_no_alloc.argtypes = [ctypes.POINTER(EncParams), vp, vp, vp, sz, ctypes.POINTER(sz)]
             L.rlfc_free_host.argtypes = [vp]
             L.rlfc_free_host.restype = None
@@ -116,6 +121,13 @@ def lib():
             L.rlfc_server_now.restype = ctypes.c_double
             L.rlfc_server_free.argtypes = [vp]
             L.rlfc_server_free.restype = None
+            i32, f32 = ctypes.c_int32, ctypes.c_float
+            L.rlfc_ks_search.argtypes = [vp, sz, u32, i32, u32, vp, vp]
+            L.rlfc_ks_compact.argtypes = [vp, sz, vp, vp, vp]
+            L.rlfc_ks_features.argtypes = [vp, vp, vp, sz, vp, vp, vp]
+            L.rlfc_mlp_loss_grad.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp]
+            L.rlfc_mlp_adam.argtypes = [vp, vp, vp, vp, vp, f32, f32, f32, f32, f32, u32, vp]
+            L.rlfc_mlp_predict.argtypes = [vp, vp, sz, vp, vp, vp]
             L.rlfc_trace_enable.argtypes = [ctypes.c_int]
             L.rlfc_trace_read.argtypes = [ctypes.POINTER(TraceEntry), sz, ctypes.POINTER(sz), ctypes.c_int]
             _lib = L
@@ -375,9 +387,14 @@ class Server:
 
 
 def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: int = 0,
-           q: int = 0, B: int = 4, stream=None) -> bytes:
-    """Algorithm 1 on the GPU (rlfc_encode): views rgb [U*V, H, W, 3] uint8 on
-    the device -> stream bytes.  c[l] is the cluster side building level l."""
+           q: int = 0, B: int = 4, stream=None, mode_space: int = 0, tau_err: int = 0, lam_q8: int = 0,
+           leaf_modes: torch.Tensor | None = None, leaf_resid: torch.Tensor | None = None,
+           leaf_label: torch.Tensor | None = None) -> bytes:
+    """Algorithm 1 on the GPU (rlfc_encode / rlfc_encode_ex): views rgb
+    [U*V, H, W, 3] uint8 on the device -> stream bytes.  c[l] is the cluster
+    side building level l.  mode_space 1 selects per-block (mode, shift); the
+    leaf_* device tensors ([U*V*3*nloc] uint8, [U*V*3*nloc, 16] int16) give
+    level-0 modes or receive the level-0 residuals and search labels."""
     if rgb.dim() != 4 or rgb.shape[0] != U * V or rgb.shape[-1] != 3:
         raise ValueError("rgb must be [U*V, H, W, 3]")
     p = EncParams()
@@ -385,10 +402,21 @@ def encode(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0, tau_b: 
     for l in range(1, L):
         p.c[l] = int(c[l])
     p.tau_p, p.tau_b, p.q = int(tau_p), int(tau_b), int(q)
+    p.mode_space, p.tau_err, p.lam_q8 = int(mode_space), int(tau_err), int(lam_q8)
+    nblk = U * V * 3 * ((rgb.shape[2] + 3) // 4) * ((rgb.shape[1] + 3) // 4)
+    ptrs = []
+    for t, dt, shape in ((leaf_modes, torch.uint8, nblk), (leaf_resid, torch.int16, nblk * 16),
+                         (leaf_label, torch.uint8, nblk)):
+        if t is None:
+            ptrs.append(None)
+        else:
+            if t.numel() != shape:
+                raise ValueError("leaf tensors must hold one entry (16 for residuals) per level-0 block")
+            ptrs.append(ctypes.c_void_p(_dev(t, dt, "leaf tensor")))
     out = ctypes.c_void_p()
     n = ctypes.c_size_t()
-    _check(lib().rlfc_encode(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")),
-                             _stream_handle(stream), ctypes.byref(out), ctypes.byref(n)))
+    _check(lib().rlfc_encode_ex(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")), *ptrs,
+                                _stream_handle(stream), ctypes.byref(out), ctypes.byref(n)))
     try:
         return ctypes.string_at(out, n.value)
     finally:
