@@ -420,12 +420,17 @@ def run_batching(args):
     from paper_1805_06019_gb300 import rlfc
 
     torch.cuda.set_device(0)
-    p = lf_synth.PRESETS["batching"]
+    p = dict(lf_synth.PRESETS["batching"])
     tau = args.tau if args.tau is not None else p["taus"][0]
     n = args.n_requests or p["n_requests"]
     U, V = p["U"], p["V"]
     t0 = time.time()
-    lf = lf_synth.preset_lightfield("batching")
+    if args.view_size and args.view_size != p["W"]:
+        # the same scene and tree at a smaller view size (profiling case)
+        p["W"] = p["H"] = args.view_size
+        lf = lf_synth.make_lightfield(U, V, p["W"], p["H"], p["disparities"], p["sigma"], p["id"], True)
+    else:
+        lf = lf_synth.preset_lightfield("batching")
     t_synth = time.time() - t0
     d_lf = torch.from_numpy(lf).cuda()
     data = rlfc.encode(d_lf, U, V, p["L"], p["c"], tau_p=tau, tau_b=16 * tau)
@@ -756,6 +761,7 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=1, help="render calls queued per stream")
     ap.add_argument("--serve-pool", type=int, default=48, help="pinned destinations per view size")
     ap.add_argument("--n-requests", type=int, default=None)
+    ap.add_argument("--view-size", type=int, default=None, help="batching: view side (default 1024)")
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--lam-q8", type=int, default=256, help="distortion weight of the mode search, /256")
     ap.add_argument("--cpu-sample-requests", type=int, default=200000)
