@@ -11,9 +11,11 @@
 //     thread decodes whole blocks with a sequential bit reader; the levels are
 //     then added top-down: reconstruction = parent reconstruction (or top
 //     RKV) + residual;
-//  3. the views (leaves), kLeafBatch at a time: compacted, decoded the same
-//     way into a residual buffer, then parent + residual is converted from
-//     YCoCg-R to RGB and written as whole image rows with 16-byte stores.
+//  3. the views (leaves), as many at a time (up to kLeafMax) as have at most
+//     kResCap stored blocks over the strip: compacted, decoded the same way
+//     into compact slots (a per-(view, record) map points at them; absent
+//     blocks add nothing), then parent + residual is converted from YCoCg-R
+//     to RGB and written as whole image rows with 16-byte stores.
 // Every stored block of the strip is decoded once and every output byte is
 // written once.
 //
@@ -33,8 +35,12 @@ namespace {
 constexpr int kStrip = 16;       // block locations per CTA
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kLeafBatch = 16;
+constexpr int kLeafMax = 64;      // views per leaf batch at most
+constexpr int kResCap = 1024;     // stored leaf blocks decoded per batch at most
 constexpr int kRecs = 3 * kStrip;
+constexpr int kLS = 52;                 // int16 per location in a node slab (48 used; 26 words keep
+                                        // a half-warp's 8-byte reads on distinct banks)
+constexpr int kSlab = kStrip * kLS;     // int16 per node: [location][channel * 16 + value]
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
@@ -49,17 +55,20 @@ struct Args {
     uint32_t S, n_int, n_top, L, q, MW;
     uint32_t nlx, nloc, W, H;
     uint32_t out_aligned16; // output base is 16-byte aligned
+    uint32_t out_aligned4;  // output base is 4-byte aligned
     uint32_t pmax;          // largest number of stored blocks in one record
     uint32_t list_cap;      // work-list capacity (items)
 };
 
 struct Smem {
     uint32_t *node;    // [S]
-    int16_t *top;      // [n_top][48][kStrip]
-    int16_t *inter;    // [n_int][48][kStrip]  internal reconstructions
-    int16_t *res;      // [kLeafBatch][48][kStrip]  leaf residuals
-    uint8_t *rgb;      // [kWarps][row bytes]: one output row per warp
+    int16_t *top;      // [n_top][kSlab]
+    int16_t *inter;    // [n_int][kSlab]  internal reconstructions
+    int16_t *res;      // [kResCap][16]  decoded leaf blocks, one slot per listed block
+    uint16_t *map;     // [kLeafMax][kRecs]  slot of (leaf, record), 0xFFFF = not stored
+    uint16_t *leafcnt; // [S - n_int]  stored blocks of each leaf over the strip
     uint32_t *mask;    // [kRecs][MW]
+    uint32_t *mpre;    // [kRecs][MW]  stored blocks in front of each mask word
     void *off;         // [kRecs][pmax]  payload bit offset of each stored block (OffT)
     uint2 *list;       // [list_cap]  (node | record << 16, rank)
 };
@@ -76,14 +85,18 @@ __device__ __forceinline__ Smem carve(const Args &a)
     m.node = reinterpret_cast<uint32_t *>(p);
     p += r16(4ull * a.S);
     m.top = reinterpret_cast<int16_t *>(p);
-    p += r16(2ull * a.n_top * 48 * kStrip);
+    p += r16(2ull * a.n_top * kSlab);
     m.inter = reinterpret_cast<int16_t *>(p);
-    p += r16(2ull * a.n_int * 48 * kStrip);
+    p += r16(2ull * a.n_int * kSlab);
     m.res = reinterpret_cast<int16_t *>(p);
-    p += r16(2ull * kLeafBatch * 48 * kStrip);
-    m.rgb = p;
-    p += r16((size_t)kWarps * kStrip * 16);
+    p += r16(32ull * kResCap);
+    m.map = reinterpret_cast<uint16_t *>(p);
+    p += r16(2ull * kLeafMax * kRecs);
+    m.leafcnt = reinterpret_cast<uint16_t *>(p);
+    p += r16(2ull * a.S);
     m.mask = reinterpret_cast<uint32_t *>(p);
+    p += r16(4ull * kRecs * a.MW);
+    m.mpre = reinterpret_cast<uint32_t *>(p);
     p += r16(4ull * kRecs * a.MW);
     m.off = p;
     p += r16(sizeof(OffT) * kRecs * a.pmax);
@@ -94,9 +107,9 @@ __device__ __forceinline__ Smem carve(const Args &a)
 inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap,
                          size_t off_size)
 {
-    return r16(4ull * S) + r16(2ull * n_top * 48 * kStrip) + r16(2ull * n_int * 48 * kStrip) +
-           r16(2ull * kLeafBatch * 48 * kStrip) + r16((size_t)kWarps * kStrip * 16) +
-           r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap);
+    return r16(4ull * S) + r16(2ull * n_top * kSlab) + r16(2ull * n_int * kSlab) +
+           r16(32ull * kResCap) + r16(2ull * kLeafMax * kRecs) + r16(2ull * S) +
+           r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap);
 }
 
 // Stored blocks of nodes [p0, p1) over the strip's records, compacted into the
@@ -116,15 +129,12 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
         if (i < pairs) {
             p = p0 + i / kRecs;
             r = i % kRecs;
-            const uint32_t *mk = m.mask + r * a.MW;
-            present = (mk[p >> 5] >> (p & 31u)) & 1u;
+            const uint32_t word = m.mask[r * a.MW + (p >> 5)];
+            present = (word >> (p & 31u)) & 1u;
             if (present && use_mask)
                 present = a.needed[node_view(m.node[p])] != 0;
-            if (present) {
-                for (uint32_t w = 0; w < (p >> 5); w++)
-                    rank += __popc(mk[w]);
-                rank += __popc(mk[p >> 5] & ((1u << (p & 31u)) - 1u));
-            }
+            if (present)
+                rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
         }
         const unsigned bal = __ballot_sync(kFullMask, present);
         uint32_t base = 0;
@@ -138,35 +148,105 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
     return *s_count;
 }
 
-// Decode the listed blocks, one block per thread; the residual
-// (min + u) * 2^(q + shift) goes to the node's slot in dst:
-// dst[((node - p0) * 48 + channel * 16 + value) * kStrip + location].
+// One listed block, one thread: the residual (min + u) * 2^(q + shift) of its
+// 16 values, read with the sequential bit reader.
+template <typename OffT>
+__device__ __forceinline__ void decode_item(const Args &a, const Smem &m, const uint32_t *s_mode, uint2 it,
+                                            uint32_t b0, int32_t val[kVals])
+{
+    const OffT *off = reinterpret_cast<const OffT *>(m.off);
+    const uint32_t rank = it.y, r = it.x >> 16;
+    const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
+    const BlockHeader h = unpack_header(get_bits(rec, 32 * a.MW + kHdrBits * rank, kHdrBits));
+    int32_t u[kVals];
+    bise_decode16(rec, off[r * a.pmax + rank], s_mode[h.mode], u);
+    const int32_t scale = 1 << (a.q + h.shift);
+#pragma unroll
+    for (int v = 0; v < kVals; v++)
+        val[v] = (h.min + u[v]) * scale;
+}
+
+// Internal nodes: each listed block into its node's slab,
+// dst[(node - p0) * kSlab + location * kLS + channel * 16 + value].
 template <typename OffT>
 __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
                                             uint32_t b0, uint32_t p0, int16_t *dst)
 {
-    const OffT *off = reinterpret_cast<const OffT *>(m.off);
-    const uint32_t hdr0 = 32 * a.MW;
     for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         const uint2 it = m.list[i];
-        const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16, rank = it.y;
+        int32_t val[kVals];
+        decode_item<OffT>(a, m, s_mode, it, b0, val);
+        const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16;
         const uint32_t loc = r / 3, c = r - 3 * loc;
-        const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
-        const BlockHeader h = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
-        int32_t u[kVals];
-        bise_decode16(rec, off[r * a.pmax + rank], s_mode[h.mode], u);
-        const int32_t scale = 1 << (a.q + h.shift);
-        int16_t *d = dst + ((p - p0) * 48 + c * 16) * kStrip + loc;
+        uint2 *d = reinterpret_cast<uint2 *>(dst + (p - p0) * kSlab + loc * kLS + c * 16);
 #pragma unroll
-        for (int v = 0; v < kVals; v++)
-            d[v * kStrip] = (int16_t)((h.min + u[v]) * scale);
+        for (int v = 0; v < kVals; v += 4)
+            d[v >> 2] = make_uint2(((uint32_t)val[v] & 0xFFFFu) | ((uint32_t)val[v + 1] << 16),
+                                   ((uint32_t)val[v + 2] & 0xFFFFu) | ((uint32_t)val[v + 3] << 16));
     }
+}
+
+// Leaves: listed block i into compact slot i (16 int16, two 16-byte stores).
+template <typename OffT>
+__device__ __forceinline__ void decode_leaf_list(const Args &a, const Smem &m, const uint32_t *s_mode,
+                                                 uint32_t count, uint32_t b0)
+{
+    for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
+        int32_t val[kVals];
+        decode_item<OffT>(a, m, s_mode, m.list[i], b0, val);
+        uint32_t w[8];
+#pragma unroll
+        for (int v = 0; v < kVals; v += 2)
+            w[v >> 1] = ((uint32_t)val[v] & 0xFFFFu) | ((uint32_t)val[v + 1] << 16);
+        uint4 *d = reinterpret_cast<uint4 *>(m.res + (size_t)i * kVals);
+        d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+// Stored blocks of leaves [p0, p1) over the strip's records, compacted into
+// the work list (slot = list position); map[(p - p0) * kRecs + r] receives
+// the slot of (leaf p, record r) or 0xFFFF.  Returns the item count.
+__device__ __forceinline__ uint32_t build_leaf_list(const Args &a, const Smem &m, uint32_t p0, uint32_t p1,
+                                                    uint32_t *s_count, bool use_mask)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0)
+        *s_count = 0;
+    __syncthreads();
+    const uint32_t pairs = (p1 - p0) * kRecs;
+    for (uint32_t i0 = 0; i0 < pairs; i0 += kThreads) {
+        const uint32_t i = i0 + tid;
+        bool present = false;
+        uint32_t p = 0, r = 0, rank = 0;
+        if (i < pairs) {
+            p = p0 + i / kRecs;
+            r = i % kRecs;
+            const uint32_t word = m.mask[r * a.MW + (p >> 5)];
+            present = (word >> (p & 31u)) & 1u;
+            if (present && use_mask)
+                present = a.needed[node_view(m.node[p])] != 0;
+            if (present)
+                rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
+        }
+        const unsigned bal = __ballot_sync(kFullMask, present);
+        uint32_t base = 0;
+        if (lane == 0 && bal)
+            base = atomicAdd(s_count, (uint32_t)__popc(bal));
+        base = __shfl_sync(kFullMask, base, 0);
+        const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
+        if (present)
+            m.list[slot] = make_uint2(p | (r << 16), rank);
+        if (i < pairs)
+            m.map[i] = present ? (uint16_t)slot : (uint16_t)0xFFFFu;
+    }
+    __syncthreads();
+    return *s_count;
 }
 
 template <bool kPacked, typename OffT>
 __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
 {
-    constexpr uint32_t kRowBytes = kPacked ? kStrip * 16 : kStrip * 12;
     __shared__ uint32_t s_mode[kNumModes];
     __shared__ uint32_t s_count;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -182,9 +262,9 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
         m.node[i] = a.node_info[i];
     for (uint32_t i = tid; i < a.n_top * kStrip * 48; i += kThreads) {
         const uint32_t t = i / (kStrip * 48), rest = i - t * kStrip * 48, loc = rest / 48, cv = rest - loc * 48;
-        m.top[(t * 48 + cv) * kStrip + loc] = loc < nl ? a.top[((size_t)t * a.nloc + b0 + loc) * 48 + cv] : 0;
+        m.top[t * kSlab + loc * kLS + cv] = loc < nl ? a.top[((size_t)t * a.nloc + b0 + loc) * 48 + cv] : 0;
     }
-    for (uint32_t i = tid; i < a.n_int * 48 * kStrip / 2; i += kThreads)
+    for (uint32_t i = tid; i < a.n_int * kSlab / 2; i += kThreads)
         reinterpret_cast<uint32_t *>(m.inter)[i] = 0;
     __syncthreads();
 
@@ -202,9 +282,13 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
         uint32_t P = 0;
         for (uint32_t w0 = 0; w0 < a.MW; w0 += 32) {
             const uint32_t word = w0 + lane < a.MW ? rec[w0 + lane] : 0u;
-            if (w0 + lane < a.MW)
+            const uint32_t cnt = (uint32_t)__popc(word);
+            const uint32_t incl = warp_inclusive_scan(cnt, lane);
+            if (w0 + lane < a.MW) {
                 mk[w0 + lane] = word;
-            P += __reduce_add_sync(kFullMask, (uint32_t)__popc(word));
+                m.mpre[r * a.MW + w0 + lane] = P + incl - cnt;
+            }
+            P += __shfl_sync(kFullMask, incl, 31);
         }
         uint32_t run = hdr0 + kHdrBits * P;
         for (uint32_t h0 = 0; h0 < P; h0 += 32) {
@@ -229,88 +313,111 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
             while (p1 < a.n_int && node_level(m.node[p1]) == lvl)
                 p1++;
             const bool from_top = lvl + 2 == a.L;
-            for (uint32_t i = tid; i < (p1 - p0) * 48 * kStrip; i += kThreads) {
-                const uint32_t p = p0 + i / (48 * kStrip), rest = i % (48 * kStrip);
+            for (uint32_t i = tid; i < (p1 - p0) * kSlab; i += kThreads) {
+                const uint32_t p = p0 + i / kSlab, rest = i % kSlab;
                 const uint32_t par = node_parent(m.node[p]);
                 const int16_t *src = from_top ? m.top : m.inter;
-                m.inter[p * 48 * kStrip + rest] += src[par * 48 * kStrip + rest];
+                m.inter[p * kSlab + rest] += src[par * kSlab + rest];
             }
             __syncthreads();
             p0 = p1;
         }
     }
 
-    // ---- phase 3: the views, kLeafBatch at a time
-    const bool fast_rows = a.out_aligned16 && (a.W % (kPacked ? 4 : 16) == 0) && nl == kStrip &&
-                           bx0 * 4 + kStrip * 4 <= a.W;
-    for (uint32_t p0 = a.n_int; p0 < a.S; p0 += kLeafBatch) {
-        const uint32_t nb = min((uint32_t)kLeafBatch, a.S - p0);
-        for (uint32_t i = tid; i < kLeafBatch * 48 * kStrip / 2; i += kThreads)
-            reinterpret_cast<uint32_t *>(m.res)[i] = 0;
-        const uint32_t cnt = build_list(a, m, p0, p0 + nb, &s_count, kPacked && a.needed != nullptr);
-        decode_list<OffT>(a, m, s_mode, cnt, b0, p0, m.res);
+    // ---- phase 3: the views, in batches of up to kLeafMax views whose stored
+    // blocks fit the kResCap decode slots
+    const bool use_mask = kPacked && a.needed != nullptr;
+    for (uint32_t p = a.n_int + tid; p < a.S; p += kThreads) {
+        uint32_t cnt = 0;
+        if (!use_mask || a.needed[node_view(m.node[p])])
+            for (uint32_t r = 0; r < kRecs; r++)
+                cnt += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
+        m.leafcnt[p - a.n_int] = (uint16_t)cnt;
+    }
+    __shared__ uint32_t s_p1;
+    for (uint32_t p0 = a.n_int; p0 < a.S;) {
         __syncthreads();
-        // parent + residual -> RGB, one (leaf, pixel row) per warp step;
-        // lane = (location, pixel pair)
-        for (uint32_t job = warp; job < nb * 4; job += kWarps) {
-            const uint32_t j = job >> 2, row = job & 3;
-            const uint32_t info = m.node[p0 + j];
-            const uint32_t view = node_view(info);
-            if (kPacked && a.needed && !a.needed[view])
-                continue;
-            const uint32_t par = node_parent(info);
-            const int16_t *base = (a.L == 2 ? m.top : m.inter) + par * 48 * kStrip;
-            const int16_t *rs = m.res + j * 48 * kStrip;
-            uint8_t *srow = m.rgb + warp * kRowBytes;
-            const uint32_t loc = lane >> 1, x2 = (lane & 1) * 2;
-            if (loc < nl) {
-                uint32_t px[2];
-#pragma unroll
-                for (int x = 0; x < 2; x++) {
-                    const uint32_t k = row * 4 + x2 + x;
-                    const int yy = base[k * kStrip + loc] + rs[k * kStrip + loc];
-                    const int co = base[(16 + k) * kStrip + loc] + rs[(16 + k) * kStrip + loc];
-                    const int cg = base[(32 + k) * kStrip + loc] + rs[(32 + k) * kStrip + loc];
-                    px[x] = ycocg_to_rgb24(yy, co, cg);
-                }
-                if (kPacked) {
-                    reinterpret_cast<uint2 *>(srow)[lane] = make_uint2(px[0], px[1]);
-                } else {
-                    uint16_t *w = reinterpret_cast<uint16_t *>(srow + lane * 6);
-                    w[0] = (uint16_t)px[0];
-                    w[1] = (uint16_t)((px[0] >> 16) | (px[1] << 8));
-                    w[2] = (uint16_t)(px[1] >> 8);
-                }
+        if (warp == 0) {
+            // the longest run of views from p0 whose stored blocks fit
+            uint32_t sum = 0, p1 = p0;
+            const uint32_t lim = min(a.S, p0 + kLeafMax);
+            for (uint32_t q0 = p0; q0 < lim; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const uint32_t c = q < lim ? m.leafcnt[q - a.n_int] : (uint32_t)kResCap + 1;
+                const uint32_t incl = warp_inclusive_scan(c, lane);
+                const unsigned ok = __ballot_sync(kFullMask, sum + incl <= (uint32_t)kResCap);
+                const uint32_t n_ok = __popc(ok);
+                if (n_ok)
+                    sum += __shfl_sync(kFullMask, incl, n_ok - 1);
+                p1 = q0 + n_ok;
+                if (n_ok < 32)
+                    break;
             }
-            __syncwarp();
-            const uint32_t y = by * 4 + row, x0 = bx0 * 4;
-            if (y < a.H && x0 < a.W) {
-                if (kPacked) {
-                    uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)view * a.H + y) * a.W + x0;
-                    const uint32_t *src = reinterpret_cast<const uint32_t *>(srow);
-                    if (fast_rows) {
-                        if (lane < kStrip)
-                            reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(src)[lane];
-                    } else {
-                        const uint32_t npx = min(nl * 4, a.W - x0);
-                        for (uint32_t b = lane; b < npx; b += 32)
-                            dst[b] = src[b];
-                    }
-                } else {
-                    uint8_t *dst = a.out + (((size_t)view * a.H + y) * a.W + x0) * 3;
-                    if (fast_rows) {
-                        if (lane < kStrip * 12 / 16)
-                            reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(srow)[lane];
-                    } else {
-                        const uint32_t nbytes = min(nl * 4, a.W - x0) * 3;
-                        for (uint32_t b = lane; b < nbytes; b += 32)
-                            dst[b] = srow[b];
-                    }
-                }
-            }
-            __syncwarp();
+            if (lane == 0)
+                s_p1 = max(p1, p0 + 1);
         }
         __syncthreads();
+        const uint32_t p1 = s_p1, nb = p1 - p0;
+        const uint32_t cnt = build_leaf_list(a, m, p0, p1, &s_count, use_mask);
+        decode_leaf_list<OffT>(a, m, s_mode, cnt, b0);
+        __syncthreads();
+        // parent + residual -> RGB: one (view, pair of block rows) per warp
+        // step, lane = (row of the pair, location), four pixels per lane
+        // written straight to the output row
+        for (uint32_t job = warp; job < nb * 2; job += kWarps) {
+            const uint32_t j = job >> 1;
+            const uint32_t info = m.node[p0 + j];
+            const uint32_t view = node_view(info);
+            if (use_mask && !a.needed[view])
+                continue;
+            const uint32_t row = (job & 1) * 2 + (lane >> 4), loc = lane & 15u;
+            const uint32_t y = by * 4 + row, x = (bx0 + loc) * 4;
+            if (loc >= nl || y >= a.H)
+                continue;
+            const int16_t *base = (a.L == 2 ? m.top : m.inter) + node_parent(info) * kSlab + loc * kLS + row * 4;
+            int32_t ycc[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const uint2 pb = *reinterpret_cast<const uint2 *>(base + c * 16);
+                const uint32_t slot = m.map[j * kRecs + loc * 3 + c];
+                const uint2 rb = slot != 0xFFFFu ? *reinterpret_cast<const uint2 *>(m.res + slot * kVals + row * 4)
+                                                 : make_uint2(0u, 0u);
+                ycc[c][0] = (int32_t)(int16_t)(pb.x & 0xFFFFu) + (int32_t)(int16_t)(rb.x & 0xFFFFu);
+                ycc[c][1] = (int32_t)(int16_t)(pb.x >> 16) + (int32_t)(int16_t)(rb.x >> 16);
+                ycc[c][2] = (int32_t)(int16_t)(pb.y & 0xFFFFu) + (int32_t)(int16_t)(rb.y & 0xFFFFu);
+                ycc[c][3] = (int32_t)(int16_t)(pb.y >> 16) + (int32_t)(int16_t)(rb.y >> 16);
+            }
+            uint32_t px[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                px[k] = ycocg_to_rgb24(ycc[0][k], ycc[1][k], ycc[2][k]);
+            const bool whole = x + 4 <= a.W;
+            if (kPacked) {
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)view * a.H + y) * a.W + x;
+                if (whole && a.out_aligned16 && (a.W & 3u) == 0) {
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
+                } else {
+                    for (uint32_t k = 0; k < 4 && x + k < a.W; k++)
+                        dst[k] = px[k];
+                }
+            } else {
+                uint8_t *dst = a.out + (((size_t)view * a.H + y) * a.W + x) * 3;
+                if (whole && a.out_aligned4 && (a.W & 3u) == 0) {
+                    // 4 pixels = 12 bytes = 3 words at a 4-byte boundary
+                    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+                    d[0] = (px[0] & 0xFFFFFFu) | (px[1] << 24);
+                    d[1] = ((px[1] >> 8) & 0xFFFFu) | (px[2] << 16);
+                    d[2] = ((px[2] >> 16) & 0xFFu) | (px[3] << 8);
+                } else {
+                    for (uint32_t k = 0; k < 4 && x + k < a.W; k++) {
+                        dst[3 * k] = (uint8_t)px[k];
+                        dst[3 * k + 1] = (uint8_t)(px[k] >> 8);
+                        dst[3 * k + 2] = (uint8_t)(px[k] >> 16);
+                    }
+                }
+            }
+        }
+        p0 = p1;
     }
 }
 
@@ -336,8 +443,9 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.W = s->info.W;
     a.H = s->info.H;
     a.out_aligned16 = ((uintptr_t)d_out & 15u) == 0;
+    a.out_aligned4 = ((uintptr_t)d_out & 3u) == 0;
     a.pmax = std::max<uint32_t>(s->max_present, 1);
-    a.list_cap = kRecs * std::max<uint32_t>(t.n_int, kLeafBatch);
+    a.list_cap = std::max<uint32_t>(kRecs * t.n_int, kResCap);
     // payload offsets are bit positions inside one record: 16 bits suffice
     // unless a record reaches 2^16 bits
     const bool off16 = (uint64_t)s->max_record_words * 32 < 65536;
