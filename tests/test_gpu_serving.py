@@ -72,9 +72,11 @@ def test_each_result_is_the_same_alone_and_in_the_mix(fleet):
     reqs = _requests(lfs, 96, seed=31)
     alone, comps_alone = _serve(rl, lfs, reqs, n_streams=1, max_batch=1, memory_budget=1 << 26)
     assert all(c["batch"] == 1 and c["status"] == 0 for c in comps_alone)
-    # a burst of Poisson arrivals at ~20k requests/s, a budget of a few
-    # views, three streams: requests wait for memory, share calls and overlap
+    # a burst of 48 requests, then Poisson arrivals at ~20k requests/s; a
+    # budget of a few views and three streams: requests wait for memory and
+    # for a free stream, share calls and overlap
     gaps = np.diff(np.concatenate([[0.0], lf_synth.poisson_arrivals(20000.0, len(reqs), preset_id=31)]))
+    gaps[:48] = 0.0
     budget = 6 * (72 * 44 * 12 + 12)
     mixed, comps = _serve(rl, lfs, reqs, gaps=gaps, n_streams=3, max_batch=8, memory_budget=budget)
     assert len(comps) == len(reqs) and all(c["status"] == 0 for c in comps)
