@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     uint32_t words = 0;
                     int bx0 = INT_MAX, by0 = INT_MAX, bx1 = INT_MIN, by1 = INT_MIN;
                     for (int k = 0; k < 4; k++) {
-                        words += window_words(tw, th, oxh[k] - oxl[k], oyh[k] - oyl[k]);
+                        words += window_words(tw, kTH, oxh[k] - oxl[k], oyh[k] - oyl[k]);
                         if (!used[k])
                             continue;
                         bx0 = min(bx0, min(max(tx0 + oxl[k], 0), (int)a.W - 1) / kBlock);
@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     wn.wx0 = tx0 + s_oxmin[k];
                     wn.wy0 = ty0 + s_oymin[k];
                     wn.WX = tw + 1 + s_oxmax[k] - s_oxmin[k];
-                    wn.WY = th + 1 + s_oymax[k] - s_oymin[k];
+                    // full tile height even for a partial tile: the rows past
+                    // the image repeat its last row, and the blend loop then
+                    // reads every row it steps through without a bounds test
+                    wn.WY = kTH + 1 + s_oymax[k] - s_oymin[k];
                     wn.FW = wn.WX + 1;
                     wn.cx0 = min(max(wn.wx0, 0), (int)a.W - 1);
                     wn.cx1 = min(max(wn.wx0 + wn.WX - 1, 0), (int)a.W - 1);
@@ -555,8 +558,6 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     }
 #pragma unroll
                     for (int rr = 0; rr < kRows; rr++) {
-                        if (r0 + rr >= th)
-                            break;   // the window holds rows up to th + spread only
                         f += fw;
                         const uint2 p0 = f[0], p1 = f[1];
                         const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&p0.x));
