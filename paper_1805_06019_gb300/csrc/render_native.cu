@@ -124,7 +124,7 @@ struct Window {
 // Per view of the current group: the four neighbours' stencil weights (blend
 // weight / 255 times the bilinear weights; all zero for an unused neighbour)
 // and integer shifts.
-struct ViewP {
+struct __align__(16) ViewP {
     float w[4][4];            // [k][00, 10, 01, 11]
     int base[4];              // sample (0, 0) of the view's 2 x 2 stencil in window k
     int16_t ox[4], oy[4];
@@ -529,6 +529,13 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
             // of kRows rows, sliding the 2 x 2 stencil down the window
             const int col = tid % kTW, r0 = (tid / kTW) * kRows;
             const bool active = col < tw && r0 < th;
+            int win_fw[4];
+            const uint2 *win_at[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                win_fw[k] = s_win[k].FW;
+                win_at[k] = reinterpret_cast<const uint2 *>(g_dyn + s_win[k].f_off) + r0 * win_fw[k] + col;
+            }
             for (int q = g0; q < ge; q++) {
                 if (!active)
                     continue;
@@ -537,13 +544,14 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
 #pragma unroll
                 for (int rr = 0; rr < kRows; rr++)
                     acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
-#pragma unroll 1
+#pragma unroll
                 for (int k = 0; k < 4; k++) {
                     if (!((vp.used >> k) & 1u))
                         continue;
-                    const float w00 = vp.w[k][0], w10 = vp.w[k][1], w01 = vp.w[k][2], w11 = vp.w[k][3];
-                    const int fw = s_win[k].FW;
-                    const uint2 *f = reinterpret_cast<const uint2 *>(g_dyn + s_win[k].f_off) + vp.base[k] + r0 * fw + col;
+                    const float4 wk = *reinterpret_cast<const float4 *>(vp.w[k]);
+                    const float w00 = wk.x, w10 = wk.y, w01 = wk.z, w11 = wk.w;
+                    const int fw = win_fw[k];
+                    const uint2 *f = win_at[k] + vp.base[k];
                     float a0[3], a1[3];
                     {
                         const uint2 p0 = f[0], p1 = f[1];
