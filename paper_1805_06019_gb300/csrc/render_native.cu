@@ -395,33 +395,59 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
 
             if (a.decoded) {
                 // ---- phase 2 (decoded views): copy the windows, clamped to the image
-                // one warp per window row, three independent loads per lane
                 const int lane = tid & 31, warp = tid >> 5;
                 int rows = 0;
                 for (int k = 0; k < 4; k++)
                     rows += s_used[k] ? s_win[k].WY : 0;
-                for (int rr = warp; rr < rows; rr += kThreads / 32) {
-                    int k = 0, r = rr;
+                // two rows per step (rows rr and rr + 8): both rows' loads are
+                // issued before either row is converted
+                auto locate = [&](int rr, int &k, int &r) {
+                    k = 0;
+                    r = rr;
                     while (!s_used[k] || r >= s_win[k].WY) {
                         r -= s_used[k] ? s_win[k].WY : 0;
                         k++;
                     }
-                    const Window &wn = s_win[k];
-                    const uint32_t *src = a.decoded + ((size_t)nview[k] * a.H + min(max(wn.wy0 + r, 0), (int)a.H - 1)) * a.W;
-                    uint2 *dst = reinterpret_cast<uint2 *>(g_dyn + wn.f_off) + r * wn.FW;
-                    for (int c0 = 0; c0 < wn.WX; c0 += 96) {
-                        uint32_t v[3];
-#pragma unroll
-                        for (int j = 0; j < 3; j++) {
-                            const int cc = c0 + lane + 32 * j;
-                            v[j] = cc < wn.WX ? __ldg(src + min(max(wn.wx0 + cc, 0), (int)a.W - 1)) : 0u;
-                        }
-#pragma unroll
-                        for (int j = 0; j < 3; j++) {
-                            const int cc = c0 + lane + 32 * j;
-                            if (cc < wn.WX)
-                                dst[cc] = rgb_half(v[j]);
-                        }
+                };
+                for (int rr = warp; rr < rows; rr += 2 * (kThreads / 32)) {
+                    const int rb = rr + kThreads / 32;
+                    const bool has_b = rb < rows;
+                    int ka, ra, kb = 0, r_b = 0;
+                    locate(rr, ka, ra);
+                    if (has_b)
+                        locate(rb, kb, r_b);
+                    const Window &wa = s_win[ka];
+                    const Window &wb = s_win[kb];
+                    const uint32_t *sa = a.decoded + ((size_t)nview[ka] * a.H + min(max(wa.wy0 + ra, 0), (int)a.H - 1)) * a.W;
+                    const uint32_t *sb = a.decoded + ((size_t)nview[kb] * a.H + min(max(wb.wy0 + r_b, 0), (int)a.H - 1)) * a.W;
+                    uint32_t va0, va1, va2, vb0 = 0u, vb1 = 0u, vb2 = 0u;
+                    va0 = lane < wa.WX ? __ldg(sa + min(max(wa.wx0 + lane, 0), (int)a.W - 1)) : 0u;
+                    va1 = lane + 32 < wa.WX ? __ldg(sa + min(max(wa.wx0 + lane + 32, 0), (int)a.W - 1)) : 0u;
+                    va2 = lane + 64 < wa.WX ? __ldg(sa + min(max(wa.wx0 + lane + 64, 0), (int)a.W - 1)) : 0u;
+                    if (has_b) {
+                        vb0 = lane < wb.WX ? __ldg(sb + min(max(wb.wx0 + lane, 0), (int)a.W - 1)) : 0u;
+                        vb1 = lane + 32 < wb.WX ? __ldg(sb + min(max(wb.wx0 + lane + 32, 0), (int)a.W - 1)) : 0u;
+                        vb2 = lane + 64 < wb.WX ? __ldg(sb + min(max(wb.wx0 + lane + 64, 0), (int)a.W - 1)) : 0u;
+                    }
+                    uint2 *da = reinterpret_cast<uint2 *>(g_dyn + wa.f_off) + ra * wa.FW;
+                    if (lane < wa.WX)
+                        da[lane] = rgb_half(va0);
+                    if (lane + 32 < wa.WX)
+                        da[lane + 32] = rgb_half(va1);
+                    if (lane + 64 < wa.WX)
+                        da[lane + 64] = rgb_half(va2);
+                    for (int cc = 96 + lane; cc < wa.WX; cc += 32)   // spreads wider than 96 pixels
+                        da[cc] = rgb_half(__ldg(sa + min(max(wa.wx0 + cc, 0), (int)a.W - 1)));
+                    if (has_b) {
+                        uint2 *db = reinterpret_cast<uint2 *>(g_dyn + wb.f_off) + r_b * wb.FW;
+                        if (lane < wb.WX)
+                            db[lane] = rgb_half(vb0);
+                        if (lane + 32 < wb.WX)
+                            db[lane + 32] = rgb_half(vb1);
+                        if (lane + 64 < wb.WX)
+                            db[lane + 64] = rgb_half(vb2);
+                        for (int cc = 96 + lane; cc < wb.WX; cc += 32)
+                            db[cc] = rgb_half(__ldg(sb + min(max(wb.wx0 + cc, 0), (int)a.W - 1)));
                     }
                 }
                 __syncthreads();
