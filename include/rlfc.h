@@ -182,15 +182,18 @@ typedef struct rlfc_batch rlfc_batch;   /* opaque, library-owned */
 typedef struct {
     uint32_t warps_per_cta;   /* 4, 8 or 16 */
     uint32_t locs_per_pop;    /* locations a warp takes from the queue at once, 1..64 */
-    uint32_t stage;           /* 1: copy a location's records to shared memory before
-                                 parsing (when they fit); 0: read them through L1 */
+    uint32_t stage;           /* 0: read a location's records through L1; 1: copy them to
+                                 shared memory before parsing; 2: copy the next location's
+                                 records (cp.async) while serving the current one (with
+                                 locs_per_pop 1); records too long for the buffers are read
+                                 through L1 */
     uint32_t graph;           /* 1: replay the call as a captured CUDA graph */
 } rlfc_batch_config;
 
 /*
  * Create a batch object for up to max_requests requests per call on stream s
  * (which must outlive it).  It allocates its device scratch (about
- * 8 B per request + 4 B per block location) on s's device, plus a private
+ * 12 B per request + 4 B per block location) on s's device, plus a private
  * CUDA stream used only to capture graphs.  The default configuration is
  * {8, 1, 0, 1}.  Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE (max_requests >=
  * 2^31), RLFC_E_UNSUPPORTED (records too large for the decoder's shared
@@ -219,7 +222,8 @@ RLFC_API int rlfc_batch_decode(rlfc_batch *b, const uint32_t *d_view, const uint
 
 /*
  * Time every candidate configuration (warps per CTA 4/8/16, locations per
- * pop 1/4, staging off/on) on these requests at level 0 with CUDA events,
+ * pop 1/4, staging 0/1, and prefetching with one location per pop) on these
+ * requests at level 0 with CUDA events,
  * keep the fastest (the graph flag is left as it was) and write it to
  * *chosen (may be NULL).  d_out and d_status receive the decoded requests.
  * Synchronises `cuda_stream`.  Errors: as rlfc_batch_decode.

@@ -7,7 +7,9 @@
 // take locations from an atomic work queue (no waits: a warp that finds the
 // queue empty exits).  For each location a warp
 //   1. optionally copies the location's three channel records (they are
-//      contiguous in the stream) into its shared-memory slice;
+//      contiguous in the stream) into its shared-memory slice, or has them
+//      copied there ahead of time (cp.async) while it serves the previous
+//      location;
 //   2. parses each record once: presence-mask popcount prefixes, then the
 //      closed-form payload length of every stored block from its 5-bit mode,
 //      turned into payload bit offsets by a warp scan;
@@ -20,6 +22,8 @@
 // The record gather (mask, headers, offsets) is paid once per location and
 // shared by every request there, which is the point of batching.
 #include <cuda_runtime.h>
+
+#include <cuda_pipeline.h>
 
 #include <algorithm>
 #include <new>
@@ -57,6 +61,7 @@ struct BinArgs {
                         // followed by the scan's per-chunk counts
     uint32_t *rank;     // [n]: position of the request inside its bin
     uint32_t *sorted;   // [n]: request indices grouped by location
+    uint32_t *sorted_view;  // [n]: their views, in the same order
     uint32_t n, n_views, nloc, aligned;
 };
 
@@ -161,8 +166,11 @@ __global__ void bin_scatter_kernel(const BinArgs a)
     if (r >= a.n)
         return;
     const uint32_t rk = a.rank[r];
-    if (rk != kBadRank)
-        a.sorted[a.cnt[a.loc[r]] + rk] = r;
+    if (rk != kBadRank) {
+        const uint32_t at = a.cnt[a.loc[r]] + rk;
+        a.sorted[at] = r;
+        a.sorted_view[at] = a.view[r];
+    }
 }
 
 struct DecArgs {
@@ -173,16 +181,22 @@ struct DecArgs {
     const uint32_t *req_view;
     const uint32_t *start;    // [nloc + 1] bin starts
     const uint32_t *sorted;
+    const uint32_t *sorted_view;
     uint8_t *out;
     uint32_t *queue;
-    uint32_t nloc, L, q, MW, level, pmax, locs_per_pop, stage_words, warp_words, aligned;
+    uint32_t nloc, L, q, MW, level, pmax, locs_per_pop, stage, stage_words, warp_words, aligned;
+    uint32_t anc_words;       // view_anc words cached in shared memory (0: read it from global)
 };
 
-// Per-warp shared-memory words for a configuration.
-__host__ __device__ inline uint32_t warp_words_for(uint32_t MW, uint32_t pmax, uint32_t L, uint32_t stage_words)
+// Per-warp shared-memory words for a configuration (the CTA adds the cached
+// ancestor table after its warps' slices).
+// stage: 0 none, 1 one buffer, 2 two buffers (prefetch); each buffer holds
+// stage_words + 4 words.
+__host__ __device__ inline uint32_t warp_words_for(uint32_t MW, uint32_t pmax, uint32_t L, uint32_t stage,
+                                                   uint32_t stage_words)
 {
     const uint32_t w = 6 * MW + 3 * pmax + kSlots * 48 + 2 * kSlots + kSlots * 3 * (L - 1) + kSlots * 16 +
-                       (stage_words ? stage_words + 2 : 0);
+                       stage * (stage_words + 4);
     return (w + 3u) & ~3u;
 }
 
@@ -192,6 +206,14 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
     __shared__ uint32_t s_modes[kNumModes];
     if (threadIdx.x < kNumModes)
         s_modes[threadIdx.x] = c_modes[threadIdx.x];
+    // the ancestor table, shared by the CTA's warps when it is small
+    const uint32_t *view_anc = a.view_anc;
+    if (a.anc_words) {
+        uint32_t *s_anc = smem + (blockDim.x >> 5) * a.warp_words;
+        for (uint32_t i = threadIdx.x; i < a.anc_words; i += blockDim.x)
+            s_anc[i] = a.view_anc[i];
+        view_anc = s_anc;
+    }
     __syncthreads();
     const int lane = (int)(threadIdx.x & 31u);
     uint32_t *s_mask = smem + (threadIdx.x >> 5) * a.warp_words;   // [3][MW]
@@ -206,23 +228,18 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
     const uint32_t nl = a.L - 1 - a.level;   // SRV levels added to the top RKV
     const uint32_t hdr0 = 32 * a.MW;
 
-    for (;;) {
-        uint32_t first = 0;
-        if (lane == 0)
-            first = atomicAdd(a.queue, a.locs_per_pop);
-        first = __shfl_sync(kFull, first, 0);
-        if (first >= a.nloc)
-            break;
-        const uint32_t last = min(first + a.locs_per_pop, a.nloc);
-        for (uint32_t loc = first; loc < last; loc++) {
+    // One location: parse its three records (from `staged` when they were
+    // copied to shared memory, else from the stream) and serve its requests.
+    auto serve = [&](uint32_t loc, const uint32_t *staged) {
+        {
             const uint32_t r0 = a.start[loc], r1 = a.start[loc + 1];
             if (r0 == r1)
-                continue;
+                return;
             const uint32_t o0 = a.offsets[3 * loc];
             const uint32_t d1 = a.offsets[3 * loc + 1] - o0, d2 = a.offsets[3 * loc + 2] - o0;
             const uint32_t span = a.offsets[3 * loc + 3] - o0;
-            const uint32_t *base = a.records + o0;
-            if (a.stage_words && span <= a.stage_words) {
+            const uint32_t *base = staged ? staged : a.records + o0;
+            if (!staged && a.stage == 1 && span <= a.stage_words) {
                 // the bit reader may touch one word past a record: copy two more
                 // (the stream carries zero padding after its last record)
                 for (uint32_t i = lane; i < span + 2; i += 32)
@@ -261,15 +278,14 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
             for (uint32_t j0 = r0; j0 < r1; j0 += kSlots) {
                 const uint32_t ns = min(kSlots, r1 - j0);
                 if ((uint32_t)lane < ns) {
-                    const uint32_t r = a.sorted[j0 + lane];
-                    s_req[lane] = r;
-                    s_view[lane] = a.req_view[r];
+                    s_req[lane] = a.sorted[j0 + lane];
+                    s_view[lane] = a.sorted_view[j0 + lane];
                 }
                 __syncwarp();
                 // ReadBlock(RKV^n, BlkIdx): the accumulators start at the top RKV
                 for (uint32_t i = lane; i < ns * 48; i += 32) {
                     const uint32_t slot = i / 48, k = i - slot * 48;
-                    const uint32_t top = a.view_anc[s_view[slot] * kMaxLevels + a.L - 1];
+                    const uint32_t top = view_anc[s_view[slot] * kMaxLevels + a.L - 1];
                     s_acc[i] = a.top[((size_t)top * a.nloc + loc) * 48 + k];
                 }
                 // stored ancestor blocks of these requests, compacted
@@ -282,7 +298,7 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
                     if (t < ntask) {
                         const uint32_t slot = t / (3 * nl), rem = t - slot * 3 * nl;
                         const uint32_t c = rem / nl, l = a.level + (rem - c * nl);
-                        const uint32_t node = a.view_anc[s_view[slot] * kMaxLevels + l];
+                        const uint32_t node = view_anc[s_view[slot] * kMaxLevels + l];
                         const uint32_t wi = node >> 5, bit = node & 31u;
                         const uint32_t word = s_mask[c * a.MW + wi];
                         pres = (word >> bit) & 1u;
@@ -336,13 +352,64 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
                 __syncwarp();
             }
         }
+    };
+
+    if (a.stage == 2) {
+        // prefetching: while a location is served, the records of the next
+        // one are copied into the warp's other buffer (cp.async)
+        uint32_t *const buf0 = s_stage, *const buf1 = s_stage + a.stage_words + 4;
+        auto pop = [&]() {
+            uint32_t v = 0;
+            if (lane == 0)
+                v = atomicAdd(a.queue, 1u);
+            return __shfl_sync(kFull, v, 0);
+        };
+        auto prefetch = [&](uint32_t loc, uint32_t *dst) {
+            if (loc >= a.nloc)
+                return false;
+            const uint32_t o0 = a.offsets[3 * loc], span = a.offsets[3 * loc + 3] - o0;
+            if (span > a.stage_words)
+                return false;
+            for (uint32_t i = lane; i < span + 2; i += 32)
+                __pipeline_memcpy_async(dst + i, a.records + o0 + i, 4);
+            return true;
+        };
+        uint32_t cur = pop();
+        bool cur_in = prefetch(cur, buf0);
+        __pipeline_commit();
+        uint32_t parity = 0;
+        while (cur < a.nloc) {
+            const uint32_t nxt = pop();
+            const bool nxt_in = prefetch(nxt, parity ? buf0 : buf1);
+            __pipeline_commit();
+            __pipeline_wait_prior(1);   // this lane's copies of `cur` are done
+            __syncwarp();               // and every lane's
+            serve(cur, cur_in ? (parity ? buf1 : buf0) : nullptr);
+            __syncwarp();               // the buffer is free for the prefetch after next
+            cur = nxt;
+            cur_in = nxt_in;
+            parity ^= 1u;
+        }
+        __pipeline_wait_prior(0);
+        return;
+    }
+    for (;;) {
+        uint32_t first = 0;
+        if (lane == 0)
+            first = atomicAdd(a.queue, a.locs_per_pop);
+        first = __shfl_sync(kFull, first, 0);
+        if (first >= a.nloc)
+            break;
+        const uint32_t last = min(first + a.locs_per_pop, a.nloc);
+        for (uint32_t loc = first; loc < last; loc++)
+            serve(loc, nullptr);
     }
 }
 
 bool valid_config(const rlfc_batch_config &c)
 {
     return (c.warps_per_cta == 4 || c.warps_per_cta == 8 || c.warps_per_cta == 16) && c.locs_per_pop >= 1 &&
-           c.locs_per_pop <= 64 && c.stage <= 1 && c.graph <= 1;
+           c.locs_per_pop <= 64 && c.stage <= 2 && c.graph <= 1;
 }
 
 }  // namespace
@@ -356,6 +423,8 @@ struct rlfc_batch {
     uint32_t *d_cnt = nullptr;      // nloc + 2 words, then one per scan chunk
     uint32_t *d_rank = nullptr;     // max_n
     uint32_t *d_sorted = nullptr;   // max_n
+    uint32_t *d_sorted_view = nullptr;   // max_n
+    uint32_t anc_words = 0;         // ancestor-table words cached per CTA (0 = none)
     rlfc_batch_config cfg{8, 1, 0, 1};
     cudaStream_t cap = nullptr;     // private stream, only ever capturing
     cudaGraphExec_t exec = nullptr;
@@ -376,8 +445,8 @@ namespace {
 
 uint32_t smem_bytes(const rlfc_batch *b, const rlfc_batch_config &c)
 {
-    return c.warps_per_cta * 4u *
-           warp_words_for(b->s->MW, b->pmax, b->s->tab.L, c.stage ? b->stage_words : 0u);
+    return c.warps_per_cta * 4u * warp_words_for(b->s->MW, b->pmax, b->s->tab.L, c.stage, b->stage_words) +
+           4u * b->anc_words;
 }
 
 bool fits(const rlfc_batch *b, const rlfc_batch_config &c) { return smem_bytes(b, c) <= b->smem_optin; }
@@ -397,6 +466,7 @@ int enqueue(rlfc_batch *b, const rlfc_batch_config &cfg, const uint32_t *view, c
     ba.cnt = b->d_cnt;
     ba.rank = b->d_rank;
     ba.sorted = b->d_sorted;
+    ba.sorted_view = b->d_sorted_view;
     ba.n = n;
     ba.n_views = s->tab.n_views;
     ba.nloc = b->nloc;
@@ -417,6 +487,8 @@ int enqueue(rlfc_batch *b, const rlfc_batch_config &cfg, const uint32_t *view, c
     da.req_view = view;
     da.start = b->d_cnt;
     da.sorted = b->d_sorted;
+    da.sorted_view = b->d_sorted_view;
+    da.anc_words = b->anc_words;
     da.out = out;
     da.queue = b->d_cnt + b->nloc + 1;
     da.nloc = b->nloc;
@@ -426,8 +498,9 @@ int enqueue(rlfc_batch *b, const rlfc_batch_config &cfg, const uint32_t *view, c
     da.level = level;
     da.pmax = b->pmax;
     da.locs_per_pop = cfg.locs_per_pop;
-    da.stage_words = cfg.stage ? b->stage_words : 0u;
-    da.warp_words = warp_words_for(s->MW, b->pmax, s->tab.L, da.stage_words);
+    da.stage = cfg.stage;
+    da.stage_words = b->stage_words;
+    da.warp_words = warp_words_for(s->MW, b->pmax, s->tab.L, cfg.stage, b->stage_words);
     da.aligned = ba.aligned;
     const uint32_t threads = cfg.warps_per_cta * 32, smem = smem_bytes(b, cfg);
     int per_sm = 0;
@@ -496,6 +569,8 @@ RLFC_API int rlfc_batch_create(const rlfc_stream *s, size_t max_requests, rlfc_b
     b->nloc = s->info.nloc_x * s->info.nloc_y;
     b->pmax = std::max<uint32_t>(s->max_present, 1u);
     b->stage_words = std::min<uint32_t>(3u * s->max_record_words, kStageCap);
+    // the ancestor table is cached per CTA up to 1024 views
+    b->anc_words = s->tab.n_views <= 1024u ? s->tab.n_views * (uint32_t)kMaxLevels : 0u;
     int v = 0;
     cudaError_t e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     b->smem_optin = e == cudaSuccess ? (uint32_t)v : 48u * 1024u;
@@ -527,6 +602,7 @@ RLFC_API int rlfc_batch_create(const rlfc_stream *s, size_t max_requests, rlfc_b
     if ((e = cudaMalloc(&b->d_cnt, (size_t)(b->nloc + 2 + chunks) * 4)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_rank, b->max_n * 4)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_sorted, b->max_n * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_sorted_view, b->max_n * 4)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         const int rc = e == cudaErrorMemoryAllocation ? RLFC_E_OOM : RLFC_E_CUDA;
         cuda_fail(e, "rlfc_batch_create");
@@ -630,7 +706,9 @@ RLFC_API int rlfc_batch_autotune(rlfc_batch *b, const uint32_t *d_view, const ui
         const uint32_t warps[3] = {4, 8, 16}, pops[2] = {1, 4};
         for (uint32_t wi = 0; wi < 3 && e == cudaSuccess && rc == RLFC_OK; wi++)
             for (uint32_t pi = 0; pi < 2 && e == cudaSuccess && rc == RLFC_OK; pi++)
-                for (uint32_t stg = 0; stg < 2 && e == cudaSuccess && rc == RLFC_OK; stg++) {
+                for (uint32_t stg = 0; stg < 3 && e == cudaSuccess && rc == RLFC_OK; stg++) {
+                    if (stg == 2 && pi != 0)
+                        continue;   // prefetching takes one location at a time
                     const rlfc_batch_config c{warps[wi], pops[pi], stg, b->cfg.graph};
                     if (!fits(b, c))
                         continue;
@@ -679,6 +757,7 @@ RLFC_API void rlfc_batch_free(rlfc_batch *b)
     cudaFree(b->d_cnt);
     cudaFree(b->d_rank);
     cudaFree(b->d_sorted);
+    cudaFree(b->d_sorted_view);
     delete b;
 }
 

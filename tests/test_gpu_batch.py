@@ -69,7 +69,7 @@ def _expected(ost, views, locs, level=0):
 
 
 CONFIGS = [dict(warps_per_cta=w, locs_per_pop=p, stage=s, graph=g)
-           for w, p, s, g in itertools.product((4, 8, 16), (1, 4), (0, 1), (0, 1))]
+           for w, p, s, g in itertools.product((4, 8, 16), (1, 4), (0, 1, 2), (0, 1))]
 
 
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
@@ -124,7 +124,8 @@ def test_crowded_locations_and_bad_requests(rl):
     locs = torch.tensor(pl, dtype=torch.int64).to(torch.uint32).cuda()
     ref_out, ref_status = st.decode_blocks(views, locs)
     b = rl.Batch(st, 1000)
-    for cfg in ({"graph": 0}, {"graph": 1, "warps_per_cta": 16, "locs_per_pop": 4, "stage": 1}):
+    for cfg in ({"graph": 0}, {"graph": 1, "warps_per_cta": 16, "locs_per_pop": 4, "stage": 1},
+                {"graph": 1, "warps_per_cta": 8, "locs_per_pop": 1, "stage": 2}):
         b.config = cfg
         out = torch.full((700, 4, 4, 3), 77, dtype=torch.uint8, device="cuda")
         status = torch.full((700,), 9, dtype=torch.uint8, device="cuda")
@@ -187,7 +188,7 @@ def test_autotune_keeps_a_valid_configuration(rl):
     b = rl.Batch(st, n)
     out = torch.empty((n, 4, 4, 3), dtype=torch.uint8, device="cuda")
     cfg = b.autotune(views, locs, out)
-    assert cfg["warps_per_cta"] in (4, 8, 16) and cfg["locs_per_pop"] in (1, 4) and cfg["stage"] in (0, 1)
+    assert cfg["warps_per_cta"] in (4, 8, 16) and cfg["locs_per_pop"] in (1, 4) and cfg["stage"] in (0, 1, 2)
     assert cfg == b.config
     want = _expected(ost, pv[:4000], pl[:4000])
     assert np.array_equal(out.cpu().numpy()[:4000], want)
