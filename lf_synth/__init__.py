@@ -40,9 +40,10 @@ PRESETS = {
                      disparities=list(np.linspace(-3.0, 3.0, 8)), sigma=1.0,
                      L=3, c=[0, 5, 4], B=4, taus=[4], n_requests=1_000_000,
                      contrast=True),
-    # 15x15 views of 625x434, lenslet-like disparities within +-1, sigma 2; 3-level (3, 5).
+    # 15x15 views of 625x434, lenslet-like disparities within +-1, sigma 2; 3-level (3, 5);
+    # threshold 3 leaves about 1.5 M level-0 blocks for the learned aid's training data.
     "learned": dict(id=3, U=15, V=15, W=625, H=434, disparities=[-1.0, -0.4, 0.3, 1.0],
-                    sigma=2.0, L=3, c=[0, 3, 5], B=4, taus=[4]),
+                    sigma=2.0, L=3, c=[0, 3, 5], B=4, taus=[3]),
     # serving light fields: 5x5x256^2, 9x9x512^2, 17x17x1024^2, 3-level each.
     "serving_small": dict(id=4, U=5, V=5, W=256, H=256, disparities=[-1.0, 0.0, 1.0],
                           sigma=1.0, L=3, c=[0, 2, 3], B=4, taus=[4]),
