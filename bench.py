@@ -301,30 +301,51 @@ def run_ours(args):
     gpu_launches = sum(l for l, _ in trace.values())
 
     # end to end through the C ABI: per-step camera upload from pinned host
-    # memory, decode + render, and download of every output to pinned memory
+    # memory, decode + render, and download of every output to pinned memory.
+    # Outputs are double-buffered so that step k's downloads (on a copy
+    # stream) overlap step k + 1's decode and render; every step's copies lie
+    # inside the timed region.
     e2e = None
     if not args.no_e2e:
         h_uv = torch.from_numpy(cams[:, :2].copy()).pin_memory()
         h_disp = torch.from_numpy(cams[:, 2].copy()).pin_memory()
-        h_lf = torch.empty(out_lf.shape, dtype=torch.uint8).pin_memory()
-        h_views = torch.empty(out_views.shape, dtype=torch.float32).pin_memory()
+        d_uv = [uv, torch.empty_like(uv)]
+        d_disp = [disp, torch.empty_like(disp)]
+        d_lf = [out_lf, torch.empty_like(out_lf)]
+        d_views = [out_views, torch.empty_like(out_views)]
+        h_lf = [torch.empty(out_lf.shape, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        h_views = [torch.empty(out_views.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        copy_st = torch.cuda.Stream()
         e_steps = min(args.steps, 5)
+        done = [None, None]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(cur)
-        for _ in range(e_steps):
-            uv.copy_(h_uv, non_blocking=True)
-            disp.copy_(h_disp, non_blocking=True)
-            st.decode_all(out_lf)
-            st.render(uv, disp, out_w, out_h, out_views)
-            h_lf.copy_(out_lf, non_blocking=True)
-            h_views.copy_(out_views, non_blocking=True)
+        for k in range(e_steps):
+            b = k & 1
+            if done[b] is not None:
+                cur.wait_event(done[b])          # buffer b's previous download finished
+            d_uv[b].copy_(h_uv, non_blocking=True)
+            d_disp[b].copy_(h_disp, non_blocking=True)
+            st.decode_all(d_lf[b])
+            st.render(d_uv[b], d_disp[b], out_w, out_h, d_views[b])
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            copy_st.wait_event(ready)
+            with torch.cuda.stream(copy_st):
+                h_lf[b].copy_(d_lf[b], non_blocking=True)
+                h_views[b].copy_(d_views[b], non_blocking=True)
+            done[b] = torch.cuda.Event()
+            done[b].record(copy_st)
+        cur.wait_stream(copy_st)
         e1.record(cur)
         torch.cuda.synchronize()
         e_ms = max_over_ranks([e0.elapsed_time(e1) / e_steps], world, "cuda")[0]
         e2e = {"value": job_mpix_per_s(world, px_lf + px_render, e_ms), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h_uv.numel() * 4 + h_disp.numel() * 4),
-               "d2h_bytes_per_step": int(h_lf.numel() + h_views.numel() * 4), "steps": e_steps}
+               "d2h_bytes_per_step": int(h_lf[0].numel() + h_views[0].numel() * 4), "steps": e_steps,
+               "note": "downloads of step k overlap step k+1 on a copy stream; the device-to-host link "
+                       "(about 193 GB/s measured on this box) bounds it"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
