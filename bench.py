@@ -305,16 +305,16 @@ def run_ours(args):
     # Outputs are double-buffered so that step k's downloads (on a copy
     # stream) overlap step k + 1's decode and render; every step's copies lie
     # inside the timed region.
-    e2e = None
-    if not args.no_e2e:
+    def end_to_end(u8: bool):
         h_uv = torch.from_numpy(cams[:, :2].copy()).pin_memory()
         h_disp = torch.from_numpy(cams[:, 2].copy()).pin_memory()
+        vdt = torch.uint8 if u8 else torch.float32
         d_uv = [uv, torch.empty_like(uv)]
         d_disp = [disp, torch.empty_like(disp)]
         d_lf = [out_lf, torch.empty_like(out_lf)]
-        d_views = [out_views, torch.empty_like(out_views)]
+        d_views = [torch.empty(out_views.shape, dtype=vdt, device="cuda") for _ in range(2)]
         h_lf = [torch.empty(out_lf.shape, dtype=torch.uint8).pin_memory() for _ in range(2)]
-        h_views = [torch.empty(out_views.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        h_views = [torch.empty(out_views.shape, dtype=vdt).pin_memory() for _ in range(2)]
         copy_st = torch.cuda.Stream()
         e_steps = min(args.steps, 5)
         done = [None, None]
@@ -341,11 +341,35 @@ def run_ours(args):
         e1.record(cur)
         torch.cuda.synchronize()
         e_ms = max_over_ranks([e0.elapsed_time(e1) / e_steps], world, "cuda")[0]
-        e2e = {"value": job_mpix_per_s(world, px_lf + px_render, e_ms), "unit": UNIT, "ms_per_step": e_ms,
-               "h2d_bytes_per_step": int(h_uv.numel() * 4 + h_disp.numel() * 4),
-               "d2h_bytes_per_step": int(h_lf[0].numel() + h_views[0].numel() * 4), "steps": e_steps,
-               "note": "downloads of step k overlap step k+1 on a copy stream; the device-to-host link "
-                       "(about 193 GB/s measured on this box) bounds it"}
+        return {"value": job_mpix_per_s(world, px_lf + px_render, e_ms), "unit": UNIT, "ms_per_step": e_ms,
+                "h2d_bytes_per_step": int(h_uv.numel() * 4 + h_disp.numel() * 4),
+                "d2h_bytes_per_step": int(h_lf[0].numel() + h_views[0].numel() * h_views[0].element_size()),
+                "steps": e_steps,
+                "note": "downloads of step k overlap step k+1 on a copy stream; the device-to-host link "
+                        "(about 193 GB/s measured on this box) bounds it"}
+
+    e2e = e2e_u8 = None
+    if not args.no_e2e:
+        e2e = end_to_end(False)
+        e2e_u8 = end_to_end(True)
+        e2e_u8["note"] = "the same step with 8-bit views (rlfc_render_views_u8), " + e2e_u8["note"]
+    # the render call with 8-bit output, device-timed like the step
+    views8 = torch.empty(out_views.shape, dtype=torch.uint8, device="cuda")
+    st.render(uv, disp, out_w, out_h, views8)
+    r8 = []
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        st.render(uv, disp, out_w, out_h, views8)
+        b.record(cur)
+        torch.cuda.synchronize()
+        r8.append(a.elapsed_time(b))
+    del views8
+    r8_ms = max_over_ranks([sum(r8) / len(r8)], world, "cuda")[0]
+    parts["render_u8"] = {"ms": r8_ms, "views_per_s": n_render / (r8_ms * 1e-3),
+                          "mpix_s": px_render / (r8_ms * 1e-3) / 1e6,
+                          "note": "rlfc_render_views_u8: the same views as 8-bit RGB (3 B/px written)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -358,6 +382,7 @@ def run_ours(args):
                 "config": _config_json(p, n_render, out_w, out_h, tau,
                                        {"stream_bytes": int(info.stream_bytes), "parallelism": f"replicas{world}"}),
                 "parts": parts, "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "e2e_u8": e2e_u8,
                 "gpu_launches": gpu_launches, "clocks": clk}
         print(json.dumps(line))
     if world > 1:

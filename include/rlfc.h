@@ -161,6 +161,17 @@ RLFC_API int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const fl
                       void *cuda_stream);
 
 /*
+ * rlfc_render_views with 8-bit output, the displayable form of the same
+ * views: d_out receives n * out_h * out_w * 3 bytes, each
+ * floor(clamp(v, 0, 1) * 255 + 0.5) of the float value v that
+ * rlfc_render_views computes (the product and the sum rounded separately in
+ * FP32).  Errors: as rlfc_render_views.
+ */
+RLFC_API int rlfc_render_views_u8(const rlfc_stream *s, const float *d_uv, const float *d_disp,
+                                  uint32_t out_w, uint32_t out_h, size_t n, uint8_t *d_out,
+                                  void *cuda_stream);
+
+/*
  * Batched random access (the paper's DecompressLFIBlock of Algorithm 2 for
  * many requests at once, Section 3.5, which notes that blocks decode in
  * parallel).  A batch object groups the requests of one call by block

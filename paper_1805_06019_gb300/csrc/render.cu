@@ -34,6 +34,7 @@ struct Args {
     const float *uv;
     const float *disp;
     float *out;
+    uint8_t *out8;      // when set, 8-bit RGB goes here instead of out
     uint32_t U, V, W, H, out_w, out_h;
     uint32_t tiles_x;
     uint32_t max_fp_blocks;  // per neighbour view
@@ -182,10 +183,7 @@ __global__ void __launch_bounds__(kThreads) render_tiled_kernel(const Args a)
             acc[c] += cam.w[k] * (((1.0f - fy) * top + fy * bot) / 255.0f);
         }
     }
-    float *o = a.out + (((size_t)n * a.out_h + y) * a.out_w + x) * 3;
-    o[0] = acc[0];
-    o[1] = acc[1];
-    o[2] = acc[2];
+    store_rgb(a.out, a.out8, ((size_t)n * a.out_h + y) * a.out_w + x, acc[0], acc[1], acc[2]);
 }
 
 // One pixel of one view, decoded by a single thread: walk the record of each
@@ -256,19 +254,16 @@ __global__ void __launch_bounds__(256) render_direct_kernel(const Args a)
             acc[c] += cam.w[k] * (((1.0f - fy) * top + fy * bot) / 255.0f);
         }
     }
-    float *o = a.out + (((size_t)n * a.out_h + y) * a.out_w + x) * 3;
-    o[0] = acc[0];
-    o[1] = acc[1];
-    o[2] = acc[2];
+    store_rgb(a.out, a.out8, ((size_t)n * a.out_h + y) * a.out_w + x, acc[0], acc[1], acc[2]);
 }
 
 }  // namespace
 
 int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
-                  uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st)
+                  uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st, uint8_t *d_out8)
 {
     if (out_w == s->info.W && out_h == s->info.H) {
-        const int rc = launch_render_native(s, d_uv, d_disp, n, d_out, st);
+        const int rc = launch_render_native(s, d_uv, d_disp, n, d_out, st, d_out8);
         if (rc != RLFC_E_UNSUPPORTED)
             return rc;
     }
@@ -286,6 +281,7 @@ int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, 
     a.uv = d_uv;
     a.disp = d_disp;
     a.out = d_out;
+    a.out8 = d_out8;
     a.U = s->info.U;
     a.V = s->info.V;
     a.W = s->info.W;

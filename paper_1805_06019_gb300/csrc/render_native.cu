@@ -52,6 +52,7 @@ struct Args {
     const float *uv;
     const float *disp;
     float *out;
+    uint8_t *out8;             // when set, 8-bit RGB goes here instead of out
     const uint32_t *decoded;   // packed RGB views [view][H][W] decoded for this call, or null
     uint32_t U, V, W, H, n;
     uint32_t tiles_x, cells_u;
@@ -611,11 +612,19 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                 for (int rr = 0; rr < kRows; rr++) {
                     if (r0 + rr >= th)
                         break;
-                    float *o = a.out + (((size_t)r * a.H + (ty0 + r0 + rr)) * a.W + (tx0 + col)) * 3;
-                    // evict-first: the outputs stream through L2 without pushing out the stream
-                    __stcs(o, acc[rr][0]);
-                    __stcs(o + 1, acc[rr][1]);
-                    __stcs(o + 2, acc[rr][2]);
+                    const size_t px = ((size_t)r * a.H + (ty0 + r0 + rr)) * a.W + (tx0 + col);
+                    if (a.out8) {
+                        uint8_t *o = a.out8 + px * 3;
+                        o[0] = to_u8(acc[rr][0]);
+                        o[1] = to_u8(acc[rr][1]);
+                        o[2] = to_u8(acc[rr][2]);
+                    } else {
+                        float *o = a.out + px * 3;
+                        // evict-first: the outputs stream through L2 without pushing out the stream
+                        __stcs(o, acc[rr][0]);
+                        __stcs(o + 1, acc[rr][1]);
+                        __stcs(o + 2, acc[rr][2]);
+                    }
                 }
             }
             g0 = ge;
@@ -646,7 +655,7 @@ __global__ void mark_needed_kernel(const Args a, uint8_t *needed)
 // Native-size rendering of n views; returns RLFC_E_UNSUPPORTED when the
 // geometry is not native (the general kernels handle it).
 int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t n, float *d_out,
-                         cudaStream_t st)
+                         cudaStream_t st, uint8_t *d_out8)
 {
     Args a;
     a.sv.records = s->d_records;
@@ -662,6 +671,7 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     a.uv = d_uv;
     a.disp = d_disp;
     a.out = d_out;
+    a.out8 = d_out8;
     a.U = s->info.U;
     a.V = s->info.V;
     a.W = s->info.W;

@@ -146,4 +146,27 @@ __device__ __forceinline__ uint32_t ycocg_to_rgb24(int y, int co, int cg)
     return (uint32_t)clamp255(r) | ((uint32_t)clamp255(g) << 8) | ((uint32_t)clamp255(b) << 16);
 }
 
+// 8-bit output of a rendered value: floor(clamp(v, 0, 1) * 255 + 0.5), the
+// product and the sum each rounded on their own (never fused), so the result
+// equals that of the same float operations anywhere else.
+__device__ __forceinline__ uint8_t to_u8(float v)
+{
+    return (uint8_t)floorf(__fadd_rn(__fmul_rn(fminf(fmaxf(v, 0.0f), 1.0f), 255.0f), 0.5f));
+}
+
+// Store a rendered RGB pixel (pixel index px) as floats, or as 8 bits when
+// out8 is set.
+__device__ __forceinline__ void store_rgb(float *out, uint8_t *out8, size_t px, float r, float g, float b)
+{
+    if (out8) {
+        out8[px * 3] = to_u8(r);
+        out8[px * 3 + 1] = to_u8(g);
+        out8[px * 3 + 2] = to_u8(b);
+    } else {
+        out[px * 3] = r;
+        out[px * 3 + 1] = g;
+        out[px * 3 + 2] = b;
+    }
+}
+
 }  // namespace rlfc

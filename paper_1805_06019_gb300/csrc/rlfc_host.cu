@@ -400,8 +400,8 @@ int rlfc_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint3
                                 (cudaStream_t)cuda_stream);
 }
 
-int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_disp,
-                      uint32_t out_w, uint32_t out_h, size_t n, float *d_out, void *cuda_stream)
+static int render_common(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
+                         uint32_t out_h, size_t n, float *d_out, uint8_t *d_out8, void *cuda_stream)
 {
     if (!s) {
         set_error("null stream");
@@ -409,7 +409,7 @@ int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_di
     }
     if (n == 0)
         return RLFC_OK;
-    if (!d_uv || !d_disp || !d_out || out_w == 0 || out_h == 0) {
+    if (!d_uv || !d_disp || (!d_out && !d_out8) || out_w == 0 || out_h == 0) {
         set_error("null argument or empty output size");
         return RLFC_E_INVALID_ARG;
     }
@@ -418,7 +418,19 @@ int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_di
         return RLFC_E_RANGE;
     }
     DeviceGuard g(s->device);
-    return launch_render(s, d_uv, d_disp, out_w, out_h, (uint32_t)n, d_out, (cudaStream_t)cuda_stream);
+    return launch_render(s, d_uv, d_disp, out_w, out_h, (uint32_t)n, d_out, (cudaStream_t)cuda_stream, d_out8);
+}
+
+int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_disp,
+                      uint32_t out_w, uint32_t out_h, size_t n, float *d_out, void *cuda_stream)
+{
+    return render_common(s, d_uv, d_disp, out_w, out_h, n, d_out, nullptr, cuda_stream);
+}
+
+int rlfc_render_views_u8(const rlfc_stream *s, const float *d_uv, const float *d_disp,
+                         uint32_t out_w, uint32_t out_h, size_t n, uint8_t *d_out, void *cuda_stream)
+{
+    return render_common(s, d_uv, d_disp, out_w, out_h, n, nullptr, d_out, cuda_stream);
 }
 
 int rlfc_encode(const rlfc_enc_params *p, const uint8_t *d_rgb, void *cuda_stream, void **host_out,

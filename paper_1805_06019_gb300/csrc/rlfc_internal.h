@@ -92,10 +92,11 @@ int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
 int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, cudaStream_t st);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
                          uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
+// d_out8: when set, 8-bit RGB output instead of d_out
 int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t n,
-                         float *d_out, cudaStream_t st);
+                         float *d_out, cudaStream_t st, uint8_t *d_out8 = nullptr);
 int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, uint32_t out_w,
-                  uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st);
+                  uint32_t out_h, uint32_t n, float *d_out, cudaStream_t st, uint8_t *d_out8 = nullptr);
 // arena: when given, every device buffer of the encoder is carved from it
 // (arena_size bytes) instead of being allocated
 // d_leaf_modes / d_leaf_resid / d_leaf_label: optional level-0 mode input and

@@ -63,7 +63,7 @@ class TraceEntry(ctypes.Structure):
 
 
 EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_decode_all",
-           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_encode", "rlfc_encode_ex", "rlfc_encode_no_alloc",
+           "rlfc_decode_blocks", "rlfc_render_views", "rlfc_render_views_u8", "rlfc_encode", "rlfc_encode_ex", "rlfc_encode_no_alloc",
            "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read",
            "rlfc_batch_create", "rlfc_batch_set_config", "rlfc_batch_get_config", "rlfc_batch_decode",
            "rlfc_batch_autotune", "rlfc_batch_free", "rlfc_server_create", "rlfc_server_add",
@@ -95,6 +95,7 @@ def lib():
             L.rlfc_decode_all.argtypes = [vp, vp, vp]
             L.rlfc_decode_blocks.argtypes = [vp, vp, vp, sz, vp, vp, vp]
             L.rlfc_render_views.argtypes = [vp, vp, vp, u32, u32, sz, vp, vp]
+            L.rlfc_render_views_u8.argtypes = [vp, vp, vp, u32, u32, sz, vp, vp]
             L.rlfc_encode.argtypes = [ctypes.POINTER(EncParams), vp, vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
             L.rlfc_encode_ex.argtypes = [ctypes.POINTER(EncParams), vp, vp, vp, vp, vp, ctypes.POINTER(vp),
                                          ctypes.POINTER(sz)]
@@ -230,14 +231,21 @@ class Stream:
         return out, status
 
     def render(self, uv: torch.Tensor, disp: torch.Tensor, out_w: int, out_h: int,
-               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        """New views: [n, out_h, out_w, 3] float32 in [0, 1] (rlfc_render_views)."""
+               out: torch.Tensor | None = None, stream=None, u8: bool = False) -> torch.Tensor:
+        """New views: [n, out_h, out_w, 3] float32 in [0, 1] (rlfc_render_views),
+        or uint8 with u8=True or a uint8 `out` (rlfc_render_views_u8)."""
         n = disp.numel()
         if uv.numel() != 2 * n:
             raise ValueError("uv must hold two floats per view")
         if out is None:
-            out = torch.empty((n, out_h, out_w, 3), dtype=torch.float32, device="cuda")
+            out = torch.empty((n, out_h, out_w, 3), dtype=torch.uint8 if u8 else torch.float32, device="cuda")
         if n == 0:
+            return out
+        if out.dtype == torch.uint8:
+            _check(lib().rlfc_render_views_u8(
+                self._h, ctypes.c_void_p(_dev(uv, torch.float32, "uv")),
+                ctypes.c_void_p(_dev(disp, torch.float32, "disp")), out_w, out_h, n,
+                ctypes.c_void_p(_dev(out, torch.uint8, "out")), _stream_handle(stream)))
             return out
         _check(lib().rlfc_render_views(
             self._h, ctypes.c_void_p(_dev(uv, torch.float32, "uv")),

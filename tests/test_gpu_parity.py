@@ -280,3 +280,33 @@ def test_plain_render_1000_views_sampled(rlfc, plain):
     # one whole view as well
     want0 = oracle.render_view(lf, p["U"], p["V"], float(cams[0, 0]), float(cams[0, 1]), float(cams[0, 2]), W, H)
     _check_render(out[0].cpu().numpy(), want0, RENDER_U8_MIN_EQUAL)
+
+
+def _u8_of_float32(x: np.ndarray) -> np.ndarray:
+    """floor(clamp(v, 0, 1) * 255 + 0.5) with each operation rounded in float32."""
+    v = np.clip(x.astype(np.float32), np.float32(0), np.float32(1))
+    return np.floor((v * np.float32(255)) + np.float32(0.5)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("name,size", [("odd_sizes_3lvl", "native"), ("four_tops", "up"), ("tiny_preset", "down"),
+                                       ("wide_strip", "native")])
+def test_render_u8_output(rlfc, name, size):
+    # the 8-bit entry point returns the 8-bit rounding of the float views
+    # (bit for bit), so it meets the same oracle bound
+    _, data, (U, V, W, H, *_rest) = _case(name)
+    lf = oracle.Stream(data).decode_all()
+    out_w, out_h = {"native": (W, H), "up": (W * 3 // 2 + 1, H * 2 - 3), "down": (max(W // 3, 1), max(H // 2, 1))}[size]
+    rng = np.random.default_rng(8)
+    n = 40 if size == "native" else 6      # 40 native views take the decode-first path
+    uv = np.stack([rng.uniform(0, U - 1, n), rng.uniform(0, V - 1, n)], axis=1).astype(np.float32)
+    disp = rng.choice([0.0, 0.7, -1.3], n).astype(np.float32)
+    st = rlfc.Stream(data)
+    d_uv, d_disp = torch.from_numpy(uv).cuda(), torch.from_numpy(disp).cuda()
+    f = st.render(d_uv, d_disp, out_w, out_h).cpu().numpy()
+    b = st.render(d_uv, d_disp, out_w, out_h, u8=True).cpu().numpy()
+    assert b.dtype == np.uint8 and b.shape == f.shape
+    assert np.array_equal(b, _u8_of_float32(f))
+    for r in range(0, n, 7):
+        want = oracle.to_u8(oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]),
+                                               out_w, out_h)).astype(np.int32)
+        assert np.abs(b[r].astype(np.int32) - want).max() <= 1
