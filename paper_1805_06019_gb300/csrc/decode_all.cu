@@ -32,13 +32,17 @@
 namespace rlfc {
 namespace {
 
-constexpr int kStrip = 16;       // block locations per CTA
-constexpr int kThreads = 512;
+constexpr int kStrip = (int)kDecodeStrip;   // block locations per CTA
+constexpr uint32_t kStageCapWords = 8192;     // strip records staged in shared memory at most
+constexpr size_t kCtaSmemTarget = 54 * 1024;  // dynamic shared memory per CTA that staging may fill up to
+                                              // (four CTAs, static shared memory and the reserve fit an SM)
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kLeafMax = 64;      // views per leaf batch at most
-constexpr int kResCap = 1024;     // stored leaf blocks decoded per batch at most
+constexpr int kResCap = 384;      // stored leaf blocks decoded per batch at most
 constexpr int kRecs = 3 * kStrip;
-constexpr int kLS = 52;                 // int16 per location in a node slab (48 used; 26 words keep
+constexpr int kRowsPerJob = 32 / kStrip;   // block rows a warp converts per step (lane = row, location)
+constexpr int kLS = 56;                 // int16 per location in a node slab (48 used; 28 words keep
                                         // a half-warp's 8-byte reads on distinct banks)
 constexpr int kSlab = kStrip * kLS;     // int16 per node: [location][channel * 16 + value]
 constexpr uint32_t kSmemBudget = 200 * 1024;
@@ -58,6 +62,7 @@ struct Args {
     uint32_t out_aligned4;  // output base is 4-byte aligned
     uint32_t pmax;          // largest number of stored blocks in one record
     uint32_t list_cap;      // work-list capacity (items)
+    uint32_t stage_words;   // shared-memory words for the strip's records (0: read them from global)
 };
 
 struct Smem {
@@ -71,6 +76,7 @@ struct Smem {
     uint32_t *mpre;    // [kRecs][MW]  stored blocks in front of each mask word
     void *off;         // [kRecs][pmax]  payload bit offset of each stored block (OffT)
     uint2 *list;       // [list_cap]  (node | record << 16, rank)
+    uint32_t *stage;   // [stage_words]  the strip's records, from a 16-byte boundary
 };
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -101,16 +107,26 @@ __device__ __forceinline__ Smem carve(const Args &a)
     m.off = p;
     p += r16(sizeof(OffT) * kRecs * a.pmax);
     m.list = reinterpret_cast<uint2 *>(p);
+    p += r16(8ull * a.list_cap);
+    m.stage = reinterpret_cast<uint32_t *>(p);
     return m;
 }
 
 inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap,
-                         size_t off_size)
+                         size_t off_size, uint32_t stage_words)
 {
     return r16(4ull * S) + r16(2ull * n_top * kSlab) + r16(2ull * n_int * kSlab) +
            r16(32ull * kResCap) + r16(2ull * kLeafMax * kRecs) + r16(2ull * S) +
-           r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap);
+           r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap) +
+           4ull * stage_words;
 }
+
+// Where record r of the strip starts: rec_base + rec_off[r] (the staged copy
+// in shared memory, or the stream).
+struct RecSrc {
+    const uint32_t *base;
+    const uint32_t *off;   // [kRecs]
+};
 
 // Stored blocks of nodes [p0, p1) over the strip's records, compacted into the
 // work list: (node | record << 16, rank).  Returns the item count.
@@ -152,11 +168,11 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
 // 16 values, read with the sequential bit reader.
 template <typename OffT>
 __device__ __forceinline__ void decode_item(const Args &a, const Smem &m, const uint32_t *s_mode, uint2 it,
-                                            uint32_t b0, int32_t val[kVals])
+                                            const RecSrc &rs, int32_t val[kVals])
 {
     const OffT *off = reinterpret_cast<const OffT *>(m.off);
     const uint32_t rank = it.y, r = it.x >> 16;
-    const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
+    const uint32_t *rec = rs.base + rs.off[r];
     const BlockHeader h = unpack_header(get_bits(rec, 32 * a.MW + kHdrBits * rank, kHdrBits));
     int32_t u[kVals];
     bise_decode16(rec, off[r * a.pmax + rank], s_mode[h.mode], u);
@@ -170,12 +186,12 @@ __device__ __forceinline__ void decode_item(const Args &a, const Smem &m, const 
 // dst[(node - p0) * kSlab + location * kLS + channel * 16 + value].
 template <typename OffT>
 __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
-                                            uint32_t b0, uint32_t p0, int16_t *dst)
+                                            const RecSrc &rs, uint32_t p0, int16_t *dst)
 {
     for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         const uint2 it = m.list[i];
         int32_t val[kVals];
-        decode_item<OffT>(a, m, s_mode, it, b0, val);
+        decode_item<OffT>(a, m, s_mode, it, rs, val);
         const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16;
         const uint32_t loc = r / 3, c = r - 3 * loc;
         uint2 *d = reinterpret_cast<uint2 *>(dst + (p - p0) * kSlab + loc * kLS + c * 16);
@@ -189,11 +205,11 @@ __device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const 
 // Leaves: listed block i into compact slot i (16 int16, two 16-byte stores).
 template <typename OffT>
 __device__ __forceinline__ void decode_leaf_list(const Args &a, const Smem &m, const uint32_t *s_mode,
-                                                 uint32_t count, uint32_t b0)
+                                                 uint32_t count, const RecSrc &rs)
 {
     for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         int32_t val[kVals];
-        decode_item<OffT>(a, m, s_mode, m.list[i], b0, val);
+        decode_item<OffT>(a, m, s_mode, m.list[i], rs, val);
         uint32_t w[8];
 #pragma unroll
         for (int v = 0; v < kVals; v += 2)
@@ -245,7 +261,7 @@ __device__ __forceinline__ uint32_t build_leaf_list(const Args &a, const Smem &m
 }
 
 template <bool kPacked, typename OffT>
-__global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
+__global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
 {
     __shared__ uint32_t s_mode[kNumModes];
     __shared__ uint32_t s_count;
@@ -266,6 +282,22 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
     }
     for (uint32_t i = tid; i < a.n_int * kSlab / 2; i += kThreads)
         reinterpret_cast<uint32_t *>(m.inter)[i] = 0;
+    // the strip's records are contiguous in the stream: stage them (from a
+    // 16-byte boundary, plus the two words the bit reader may read past a
+    // record; the stream ends in zero padding) when they fit
+    __shared__ uint32_t s_roff[kRecs];
+    const uint32_t w_lo = a.offsets[3 * b0] & ~3u;
+    const uint32_t n4 = (a.offsets[3 * (b0 + nl)] + 2 - w_lo + 3) / 4;
+    const bool staged = 4 * n4 <= a.stage_words;
+    if (staged) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.records + w_lo);
+        uint4 *dst = reinterpret_cast<uint4 *>(m.stage);
+        for (uint32_t i = tid; i < n4; i += kThreads)
+            dst[i] = src[i];
+    }
+    for (uint32_t r = tid; r < kRecs; r += kThreads)
+        s_roff[r] = r < 3 * nl ? a.offsets[3 * b0 + r] - (staged ? w_lo : 0u) : 0u;
+    const RecSrc rs{staged ? m.stage : a.records, s_roff};
     __syncthreads();
 
     // ---- phase 1: per record, the payload offset of every stored block
@@ -278,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
                 mk[w] = 0;
             continue;
         }
-        const uint32_t *rec = a.records + a.offsets[3 * b0 + r];
+        const uint32_t *rec = rs.base + rs.off[r];
         uint32_t P = 0;
         for (uint32_t w0 = 0; w0 < a.MW; w0 += 32) {
             const uint32_t word = w0 + lane < a.MW ? rec[w0 + lane] : 0u;
@@ -305,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
     // ---- phase 2: internal nodes, decoded, then reconstructed level by level
     if (a.n_int > 0) {
         const uint32_t cnt = build_list(a, m, 0, a.n_int, &s_count, false);
-        decode_list<OffT>(a, m, s_mode, cnt, b0, 0, m.inter);
+        decode_list<OffT>(a, m, s_mode, cnt, rs, 0, m.inter);
         __syncthreads();
         for (uint32_t p0 = 0; p0 < a.n_int;) {
             const uint32_t lvl = node_level(m.node[p0]);
@@ -359,18 +391,19 @@ __global__ void __launch_bounds__(kThreads) decode_all_kernel(const Args a)
         __syncthreads();
         const uint32_t p1 = s_p1, nb = p1 - p0;
         const uint32_t cnt = build_leaf_list(a, m, p0, p1, &s_count, use_mask);
-        decode_leaf_list<OffT>(a, m, s_mode, cnt, b0);
+        decode_leaf_list<OffT>(a, m, s_mode, cnt, rs);
         __syncthreads();
-        // parent + residual -> RGB: one (view, pair of block rows) per warp
-        // step, lane = (row of the pair, location), four pixels per lane
-        // written straight to the output row
-        for (uint32_t job = warp; job < nb * 2; job += kWarps) {
-            const uint32_t j = job >> 1;
+        // parent + residual -> RGB: one (view, kRowsPerJob block rows) per
+        // warp step, lane = (row, location), four pixels per lane written
+        // straight to the output row
+        constexpr uint32_t kJobsPerView = 4 / kRowsPerJob;
+        for (uint32_t job = warp; job < nb * kJobsPerView; job += kWarps) {
+            const uint32_t j = job / kJobsPerView;
             const uint32_t info = m.node[p0 + j];
             const uint32_t view = node_view(info);
             if (use_mask && !a.needed[view])
                 continue;
-            const uint32_t row = (job & 1) * 2 + (lane >> 4), loc = lane & 15u;
+            const uint32_t row = (job % kJobsPerView) * kRowsPerJob + lane / kStrip, loc = lane % kStrip;
             const uint32_t y = by * 4 + row, x = (bx0 + loc) * 4;
             if (loc >= nl || y >= a.H)
                 continue;
@@ -449,7 +482,14 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     // payload offsets are bit positions inside one record: 16 bits suffice
     // unless a record reaches 2^16 bits
     const bool off16 = (uint64_t)s->max_record_words * 32 < 65536;
-    const size_t smem = smem_bytes(a.S, a.n_top, a.n_int, a.MW, a.pmax, a.list_cap, off16 ? 2 : 4);
+    // staging for the largest strip's records (16-byte boundary, bit-reader
+    // slack), within what keeps a CTA at kCtaSmemTarget bytes; strips whose
+    // records do not fit read them from the stream
+    const size_t base = smem_bytes(a.S, a.n_top, a.n_int, a.MW, a.pmax, a.list_cap, off16 ? 2 : 4, 0);
+    const size_t room = base < kCtaSmemTarget ? (kCtaSmemTarget - base) / 4 : 0;
+    a.stage_words = (uint32_t)std::min<size_t>({(size_t)((s->max_strip_words + 8 + 3) & ~3u),
+                                                (size_t)kStageCapWords, room & ~size_t(3)});
+    const size_t smem = base + 4ull * a.stage_words;
     if (smem > kSmemBudget || a.S >= 65536) {
         set_error("tree too large for the decode-all kernel's shared memory");
         return RLFC_E_UNSUPPORTED;

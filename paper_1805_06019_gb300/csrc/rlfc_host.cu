@@ -228,10 +228,12 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
                 return fmt("record length disagrees with its blocks");
         }
     }
+    // the longest run of records of kDecodeStrip consecutive locations of a
+    // row (the full decode stages one such run per CTA)
     ps.max_strip_words = 0;
     for (uint32_t y = 0; y < ps.nly; y++)
-        for (uint32_t x0 = 0; x0 < ps.nlx; x0 += 32) {
-            const uint32_t b0 = y * ps.nlx + x0, b1 = y * ps.nlx + std::min(x0 + 32, ps.nlx);
+        for (uint32_t x0 = 0; x0 < ps.nlx; x0 += kDecodeStrip) {
+            const uint32_t b0 = y * ps.nlx + x0, b1 = y * ps.nlx + std::min(x0 + kDecodeStrip, ps.nlx);
             ps.max_strip_words = std::max(ps.max_strip_words, rd32(off + 12ull * b1) - rd32(off + 12ull * b0));
         }
     if (ps.B != 4) {

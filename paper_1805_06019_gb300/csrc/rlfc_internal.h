@@ -12,6 +12,7 @@
 namespace rlfc {
 
 constexpr int kMaxLevels = 8;
+constexpr uint32_t kDecodeStrip = 8;   // block locations per CTA of the full decode
 constexpr int kPadWords = 8;   // zero words after the records (bit-reader over-read)
 
 // Per BFS position: level (bits 0..3), parent reference (bits 4..17: the top
@@ -37,7 +38,7 @@ struct rlfc_stream {
     uint32_t MW = 0;            // mask words per record
     uint64_t record_words = 0;
     uint32_t max_record_words = 0;
-    uint32_t max_strip_words = 0;    // records of 32 consecutive locations of a row
+    uint32_t max_strip_words = 0;    // records of kDecodeStrip consecutive locations of a row
     uint32_t max_present = 0;        // most stored blocks in one record
     // device buffers
     uint32_t *d_records = nullptr;   // record_words + kPadWords
