@@ -436,11 +436,12 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
             } else {
                 uint8_t *dst = a.out + (((size_t)view * a.H + y) * a.W + x) * 3;
                 if (whole && a.out_aligned4 && (a.W & 3u) == 0) {
-                    // 4 pixels = 12 bytes = 3 words at a 4-byte boundary
+                    // 4 pixels = 12 bytes = 3 words at a 4-byte boundary, each
+                    // assembled by one byte permute of two neighbouring pixels
                     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-                    d[0] = (px[0] & 0xFFFFFFu) | (px[1] << 24);
-                    d[1] = ((px[1] >> 8) & 0xFFFFu) | (px[2] << 16);
-                    d[2] = ((px[2] >> 16) & 0xFFu) | (px[3] << 8);
+                    d[0] = __byte_perm(px[0], px[1], 0x4210);
+                    d[1] = __byte_perm(px[1], px[2], 0x5421);
+                    d[2] = __byte_perm(px[2], px[3], 0x6542);
                 } else {
                     for (uint32_t k = 0; k < 4 && x + k < a.W; k++) {
                         dst[3 * k] = (uint8_t)px[k];

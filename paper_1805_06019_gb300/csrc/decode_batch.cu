@@ -339,9 +339,9 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
                         const uint32_t slot = i / 12, wd = i - slot * 12;
                         const uint32_t p0 = (4 * wd) / 3;
                         const uint32_t lo = s_rgb[slot * 16 + p0], hi = s_rgb[slot * 16 + p0 + 1];
-                        const uint64_t two = (uint64_t)(lo & 0xFFFFFFu) | ((uint64_t)(hi & 0xFFFFFFu) << 24);
+                        const uint32_t sh = (4 * wd) % 3;   // first byte of the word inside pixel p0
                         reinterpret_cast<uint32_t *>(a.out + (size_t)s_req[slot] * 48)[wd] =
-                            (uint32_t)(two >> (8 * ((4 * wd) % 3)));
+                            __byte_perm(lo, hi, sh == 0 ? 0x4210u : (sh == 1 ? 0x5421u : 0x6542u));
                     }
                 } else {
                     for (uint32_t i = lane; i < ns * 48; i += 32) {

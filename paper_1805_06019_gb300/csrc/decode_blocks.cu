@@ -57,8 +57,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) decode_blocks_kernel(const 
         const uint32_t lo = __shfl_sync(kFullMask, rgb, min(p0, 31u));
         const uint32_t hi = __shfl_sync(kFullMask, rgb, min(p0 + 1, 31u));
         if (lane < 12) {
-            const uint64_t two = (uint64_t)(lo & 0xFFFFFFu) | ((uint64_t)(hi & 0xFFFFFFu) << 24);
-            reinterpret_cast<uint32_t *>(dst)[lane] = (uint32_t)(two >> (8 * ((lane * 4) % 3)));
+            const uint32_t sh = (uint32_t)(lane * 4) % 3;   // first byte of the word inside pixel p0
+            reinterpret_cast<uint32_t *>(dst)[lane] =
+                __byte_perm(lo, hi, sh == 0 ? 0x4210u : (sh == 1 ? 0x5421u : 0x6542u));
         }
     } else if (lane < 16) {
         dst[3 * lane] = (uint8_t)rgb;
