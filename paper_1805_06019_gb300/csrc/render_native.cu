@@ -56,6 +56,9 @@ struct Args {
     const uint32_t *decoded;   // packed RGB views [view][H][W] decoded for this call, or null
     uint32_t U, V, W, H, n;
     uint32_t tiles_x, cells_u;
+    uint32_t n_tiles;           // tiles per view
+    const uint32_t *cell_list;  // the grid cells that hold cameras, *cell_count of them
+    const uint32_t *cell_count;
     uint32_t need_max;   // distinct nodes four views can need: 4 (L - 1)
 };
 
@@ -178,12 +181,20 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
     __shared__ uint32_t s_ent_off;     // word offset of the node table
 
     const int tid = threadIdx.x;
-    const uint32_t cell = blockIdx.y;
-    const int ci = (int)(cell % a.cells_u), cj = (int)(cell / a.cells_u);
-    const int tx0 = (int)(blockIdx.x % a.tiles_x) * kTW, ty0 = (int)(blockIdx.x / a.tiles_x) * kTH;
-    const int tw = min(kTW, (int)a.W - tx0), th = min(kTH, (int)a.H - ty0);
     if (tid < kNumModes)
         s_mode[tid] = c_modes[tid];
+    // with a cell list the CTAs are persistent over (occupied cell, tile)
+    // items, cell-major so that neighbouring CTAs read the same neighbour
+    // views; otherwise a CTA is the one item (cell blockIdx.y, tile
+    // blockIdx.x)
+    const bool listed = a.cell_list != nullptr;
+    const uint32_t n_items = listed ? *a.cell_count * a.n_tiles : 1u;
+    for (uint32_t item = listed ? blockIdx.x : 0u; item < n_items; item += gridDim.x) {
+    const uint32_t cell = listed ? a.cell_list[item / a.n_tiles] : blockIdx.y;
+    const uint32_t tile = listed ? item % a.n_tiles : blockIdx.x;
+    const int ci = (int)(cell % a.cells_u), cj = (int)(cell / a.cells_u);
+    const int tx0 = (int)(tile % a.tiles_x) * kTW, ty0 = (int)(tile / a.tiles_x) * kTH;
+    const int tw = min(kTW, (int)a.W - tx0), th = min(kTH, (int)a.H - ty0);
     int nview[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -631,6 +642,44 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
             __syncthreads();
         }
     }
+    __syncthreads();   // the next item reuses the shared memory
+    }
+}
+
+// Lists the grid cells that hold at least one camera (each once; the
+// order does not matter).  One CTA: a bitmask of the cells in shared memory
+// (at most 65535 cells, 2048 words), then the set bits appended to the list.
+constexpr int kListThreads = 1024;
+constexpr uint32_t kMaxCellWords = 2048;
+
+__global__ void __launch_bounds__(kListThreads) list_cells_kernel(const Args a, uint32_t n_cells, uint32_t *list,
+                                                                  uint32_t *count)
+{
+    __shared__ uint32_t mask[kMaxCellWords];
+    __shared__ uint32_t total;
+    const uint32_t words = (n_cells + 31) / 32;
+    for (uint32_t w = threadIdx.x; w < words; w += kListThreads)
+        mask[w] = 0u;
+    if (threadIdx.x == 0)
+        total = 0u;
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < a.n; r += kListThreads) {
+        const uint32_t cell = cell_of(a, r);
+        atomicOr(&mask[cell >> 5], 1u << (cell & 31));
+    }
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < words; w += kListThreads) {
+        uint32_t bits = mask[w];
+        uint32_t at = atomicAdd(&total, (uint32_t)__popc(bits));
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            list[at++] = w * 32 + (uint32_t)b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        *count = total;
 }
 
 // Marks the neighbour views that each camera blends with a non-zero weight.
@@ -692,7 +741,30 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
                                          (int)kSmemBytes);
     if (e != cudaSuccess)
         return cuda_fail(e, "render_native: shared memory attribute");
-    dim3 grid(a.tiles_x * tiles_y, a.cells_u * cells_v);
+    a.n_tiles = a.tiles_x * tiles_y;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_native_kernel, kThreads, kSmemBytes)) !=
+            cudaSuccess)
+        return cuda_fail(e, "render_native: occupancy");
+    const uint32_t n_cells = a.cells_u * cells_v;
+    dim3 grid(a.n_tiles, n_cells);
+    uint32_t *cells = nullptr;
+    a.cell_list = nullptr;
+    a.cell_count = nullptr;
+    const uint32_t resident = (uint32_t)std::max(sms, 1) * (uint32_t)std::max(per_sm, 1);
+    if (n < 2 * n_cells && (uint64_t)a.n_tiles * n_cells >= 8ull * resident) {
+        // few cameras for a large grid: most of its CTAs would find an empty
+        // cell, so list the occupied cells and run persistent CTAs over their
+        // tiles only (list and count in stream-ordered scratch)
+        grid = dim3(resident);
+        if ((e = cudaMallocAsync(&cells, 4ull * (n_cells + 1), st)) != cudaSuccess)
+            return cuda_fail(e, "render_native: cell list");
+        a.cell_list = cells;
+        a.cell_count = cells + n_cells;
+        { rlfc::TraceScope trace_("list_cells_kernel", st); list_cells_kernel<<<1, kListThreads, 0, st>>>(a, n_cells, cells, cells + n_cells); }
+    }
     // Batches of many views decode the views they need once into a transient
     // packed-RGB buffer (stream-ordered allocation, freed on the same stream);
     // small batches decode block by block inside the render kernel.
@@ -719,11 +791,15 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
                 rc = cuda_fail(e, "render_native launch");
         }
         cudaFreeAsync(scratch, st);
+        if (cells)
+            cudaFreeAsync(cells, st);
         return rc;
     }
     cudaGetLastError();   // a failed stream-ordered allocation only selects the other path
     { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
     e = cudaGetLastError();
+    if (cells)
+        cudaFreeAsync(cells, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "render_native launch");
     return RLFC_OK;
