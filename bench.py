@@ -43,7 +43,11 @@ UNIT = "Mpix/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
 # capture of the same kernel build on this workload (config, tau, views,
 # kernel); a kernel missing here reports null
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # render_native_kernel, first timed step of `bench.py --steps 2 --warmup 1` (ncu one-pass
+    # dram__bytes_read.sum 86.70 MB + dram__bytes_write.sum 3.08 GB)
+    ("plain", 4, 1000, "render_native_kernel"): 86_700_000 + 3_080_000_000,
+}
 
 
 def _peaks():
@@ -264,6 +268,20 @@ def run_ours(args):
     rlfc.trace_enable(False)
     t_dec = [a.elapsed_time(b) for a, b, _ in evs]
     t_ren = [b.elapsed_time(c) for _, b, c in evs]
+    # the same calls back to back without the flush: warm-L2 figures beside
+    # the flushed ones (the compressed stream stays in L2 between calls)
+    wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        a, b, c = wev[k]
+        a.record(cur)
+        st.decode_all(out_lf)
+        b.record(cur)
+        st.render(uv, disp, out_w, out_h, out_views)
+        c.record(cur)
+    torch.cuda.synchronize()
+    dec_warm, ren_warm = max_over_ranks([sum(a.elapsed_time(b) for a, b, _ in wev) / args.steps,
+                                         sum(b.elapsed_time(c) for _, b, c in wev) / args.steps], world, "cuda")
     step_ms = sum(t_dec) / args.steps + sum(t_ren) / args.steps
     step_ms, dec_ms, ren_ms = max_over_ranks([step_ms, sum(t_dec) / args.steps, sum(t_ren) / args.steps],
                                              world, "cuda")
@@ -278,8 +296,9 @@ def run_ours(args):
     ren_gbs = b_ren / (ren_ms * 1e-3) / 1e9
     parts = {
         "decode_all": {"ms": dec_ms, "mpix_s": px_lf / (dec_ms * 1e-3) / 1e6, "algorithmic_bytes": b_dec,
-                       "gbs": dec_gbs, "hbm_frac": dec_gbs / peak},
-        "render": {"ms": ren_ms, "views_per_s": n_render / (ren_ms * 1e-3), "mpix_s": px_render / (ren_ms * 1e-3) / 1e6,
+                       "gbs": dec_gbs, "hbm_frac": dec_gbs / peak, "ms_warm": dec_warm},
+        "render": {"ms": ren_ms, "ms_warm": ren_warm, "views_per_s": n_render / (ren_ms * 1e-3),
+                   "mpix_s": px_render / (ren_ms * 1e-3) / 1e6,
                    "algorithmic_bytes": b_ren, "gbs": ren_gbs, "hbm_frac": ren_gbs / peak},
     }
     # per-kernel durations from the library's own CUDA events (on the
@@ -618,7 +637,8 @@ def run_serving(args):
     """Eight resident light fields (three 5x5x256^2, three 9x9x512^2, two
     17x17x1024^2), view requests at their native sizes arriving as a Poisson
     process at several rates, served with continuous batching; latency is
-    submit -> view copied to pinned host memory."""
+    submit -> view copied to pinned host memory.  Each output format (float
+    RGB, 8-bit RGB) runs the same rates."""
     import torch
     from paper_1805_06019_gb300 import rlfc
 
@@ -639,15 +659,20 @@ def run_serving(args):
     srv = rlfc.Server(n_streams=args.serve_streams, max_batch=args.serve_max_batch, memory_budget=budget,
                       max_inflight=args.serve_inflight)
     ids = [srv.add(s) for s in streams]
-    # pinned destinations, reused once their request has completed
-    pool = {}
-    for U, V, W, H, _ in grids:
-        if (W, H) not in pool:
-            pool[(W, H)] = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
-                            for _ in range(args.serve_pool)]
     rates = [float(r) for r in args.serve_rates.split(",")]
+    formats = args.serve_formats.split(",")
     results = []
-    for ri, rate in enumerate(rates):
+    pools = {}
+    for fmt, ri, rate in [(f, ri, r) for f in formats for ri, r in enumerate(rates)]:
+        # pinned destinations per format, reused once their request has completed
+        if fmt not in pools:
+            pools.clear()
+            pools[fmt] = {}
+            for U, V, W, H, _ in grids:
+                if (W, H) not in pools[fmt]:
+                    pools[fmt][(W, H)] = [torch.empty((H, W, 3), dtype=torch.uint8 if fmt == "u8" else torch.float32)
+                                          .pin_memory() for _ in range(args.serve_pool)]
+        pool = pools[fmt]
         n = max(int(rate * args.serve_seconds), 50)
         arr = lf_synth.poisson_arrivals(rate, n, preset_id=4 + ri)
         lf_i, fu, fv, fd = lf_synth.serving_requests(n, len(streams), preset_id=4 + ri)
@@ -676,20 +701,20 @@ def run_serving(args):
         lat = np.array([c["t_done"] - c["t_submit"] for c in comps]) * 1e3
         span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
         px = sum(grids[c["lf"]][2] * grids[c["lf"]][3] for c in comps)
-        results.append({"rate_req_s": rate, "requests": n, "ok": int(sum(c["status"] == 0 for c in comps)),
+        results.append({"format": fmt, "rate_req_s": rate, "requests": n, "ok": int(sum(c["status"] == 0 for c in comps)),
                         "views_per_s": len(comps) / span, "mpix_s": px / span / 1e6,
                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                         "mean_batch": float(np.mean([c["batch"] for c in comps])),
                         "client_waits_for_buffers": waited})
     srv.close()
-    top = results[-1]
+    top = [r for r in results if r["format"] == formats[0]][-1]
     line = {"metric": METRIC, "value": top["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: 8 resident light fields (3x 5x5x256^2 tau 2/4/8, 3x 9x9x512^2 "
                                    "tau 2/4/8, 2x 17x17x1024^2 tau 4/8), native-size view requests, "
                                    "Poisson arrivals; latency = submit to view in pinned host memory",
-                       "rates": rates, "seconds_per_rate": args.serve_seconds,
+                       "formats": formats, "value_format": formats[0], "rates": rates, "seconds_per_rate": args.serve_seconds,
                        "n_streams": args.serve_streams, "max_batch": args.serve_max_batch,
                        "max_inflight": args.serve_inflight,
                        "memory_budget_mib": args.serve_budget, "resident_device_bytes": resident,
@@ -806,6 +831,7 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=2048, help="MiB of outputs in flight")
     ap.add_argument("--serve-inflight", type=int, default=1, help="render calls queued per stream")
     ap.add_argument("--serve-pool", type=int, default=48, help="pinned destinations per view size")
+    ap.add_argument("--serve-formats", default="f32,u8", help="output formats served, in order (f32, u8)")
     ap.add_argument("--n-requests", type=int, default=None)
     ap.add_argument("--view-size", type=int, default=None, help="batching: view side (default 1024)")
     ap.add_argument("--epochs", type=int, default=8)

@@ -272,7 +272,7 @@ typedef struct rlfc_server rlfc_server;   /* opaque, library-owned */
 typedef struct {
     uint32_t n_streams;       /* CUDA streams calls are spread over, 1..64 */
     uint32_t max_batch;       /* views per render call, 1..4096 */
-    uint64_t memory_budget;   /* device bytes of outputs in flight (out_w*out_h*12 + 12 per view) */
+    uint64_t memory_budget;   /* device bytes of outputs in flight (out_w*out_h*12 + 12 per float view, out_w*out_h*3 + 12 per 8-bit view) */
     uint32_t max_inflight;    /* calls queued on one stream at a time, 1..64: while every stream
                                  is full, arrivals wait and then share the next call */
     uint32_t pad;
@@ -304,6 +304,15 @@ RLFC_API int rlfc_server_add(rlfc_server *srv, const rlfc_stream *s, uint32_t *l
  */
 RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
                                 uint32_t out_w, uint32_t out_h, float *host_out, uint64_t *ticket);
+
+/*
+ * As rlfc_server_submit, with the view delivered as 8-bit RGB (out_h * out_w
+ * * 3 bytes, the rounding of rlfc_render_views_u8): a quarter of the device
+ * memory and of the copy to the host.  Requests of the two formats never
+ * share a call.  Errors: as rlfc_server_submit.
+ */
+RLFC_API int rlfc_server_submit_u8(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
+                                   uint32_t out_w, uint32_t out_h, uint8_t *host_out, uint64_t *ticket);
 
 /*
  * Move up to `cap` completed requests into out (oldest first) and set *n.

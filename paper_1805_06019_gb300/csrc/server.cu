@@ -35,11 +35,13 @@ struct Req {
     uint32_t lf;
     float u, v, d;
     uint32_t w, h;
-    float *host_out;
+    uint32_t u8;          // 1: 8-bit RGB output, 0: float RGB
+    void *host_out;
     double t_submit;
 };
 
-size_t view_bytes(uint32_t w, uint32_t h) { return (size_t)w * h * 12 + 12; }
+// device bytes of one request: its view and its camera parameters
+size_t view_bytes(uint32_t w, uint32_t h, uint32_t u8) { return (size_t)w * h * (u8 ? 3 : 12) + 12; }
 
 constexpr uint32_t kParamSlots = 512;
 
@@ -113,8 +115,8 @@ void CUDART_CB on_step_done(void *p)
     delete s;
 }
 
-// Issue one render call for `reqs` (same light field and size) on stream
-// `si`; completion arrives through on_step_done.
+// Issue one render call for `reqs` (same light field, size and output
+// format) on stream `si`; completion arrives through on_step_done.
 void launch_step(rlfc_server *srv, std::vector<Req> &&reqs, size_t bytes, uint32_t slot, uint32_t si)
 {
     Step *step = new Step{srv, std::move(reqs), bytes, slot, si, RLFC_OK, now_s()};
@@ -127,18 +129,22 @@ void launch_step(rlfc_server *srv, std::vector<Req> &&reqs, size_t bytes, uint32
         par[2 * i + 1] = step->reqs[i].v;
         par[2 * n + i] = step->reqs[i].d;
     }
-    const size_t px = (size_t)w * h * 3;
-    float *d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, (px * n + 3 * (size_t)n) * sizeof(float), st);
+    // one stream-ordered allocation: the parameters, then the views
+    const size_t view = (size_t)w * h * 3 * (r0.u8 ? 1 : sizeof(float));
+    const size_t par_bytes = (3 * (size_t)n * sizeof(float) + 255) / 256 * 256;
+    uint8_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), par_bytes + view * n, st);
     int rc = RLFC_OK;
     if (e == cudaSuccess) {
-        float *d_out = d, *d_par = d + px * n;
+        float *d_par = reinterpret_cast<float *>(d);
+        uint8_t *d_view = d + par_bytes;
         e = cudaMemcpyAsync(d_par, par, 3 * (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
-            rc = launch_render(srv->lfs[r0.lf], d_par, d_par + 2 * n, w, h, n, d_out, st);
+            rc = r0.u8 ? launch_render(srv->lfs[r0.lf], d_par, d_par + 2 * n, w, h, n, nullptr, st, d_view)
+                       : launch_render(srv->lfs[r0.lf], d_par, d_par + 2 * n, w, h, n,
+                                       reinterpret_cast<float *>(d_view), st);
             for (uint32_t i = 0; i < n && rc == RLFC_OK && e == cudaSuccess; i++)
-                e = cudaMemcpyAsync(step->reqs[i].host_out, d_out + px * i, px * sizeof(float),
-                                    cudaMemcpyDeviceToHost, st);
+                e = cudaMemcpyAsync(step->reqs[i].host_out, d_view + view * i, view, cudaMemcpyDeviceToHost, st);
         }
         cudaFreeAsync(d, st);
     }
@@ -175,22 +181,23 @@ void worker_main(rlfc_server *srv)
             if (srv->queue.empty())
                 return srv->stop;
             const Req &r = srv->queue.front();
-            return srv->in_use + view_bytes(r.w, r.h) <= srv->cfg.memory_budget && !srv->free_slots.empty() &&
+            return srv->in_use + view_bytes(r.w, r.h, r.u8) <= srv->cfg.memory_budget && !srv->free_slots.empty() &&
                    pick_stream(srv) >= 0;
         });
         if (srv->queue.empty() && srv->stop)
             break;
         // admit in arrival order while the outputs fit; group by (light
-        // field, size), keeping the order inside each group
-        std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<Req>> groups;
-        std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> order;
+        // field, size, format), keeping the order inside each group
+        using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>;
+        std::map<Key, std::vector<Req>> groups;
+        std::vector<Key> order;
         size_t admitted = 0;
         while (!srv->queue.empty()) {
             const Req &r = srv->queue.front();
-            const size_t b = view_bytes(r.w, r.h);
+            const size_t b = view_bytes(r.w, r.h, r.u8);
             if (srv->in_use + admitted + b > srv->cfg.memory_budget)
                 break;
-            const auto key = std::make_tuple(r.lf, r.w, r.h);
+            const Key key = std::make_tuple(r.lf, r.w, r.h, r.u8);
             auto it = groups.find(key);
             if (it == groups.end()) {
                 order.push_back(key);
@@ -216,7 +223,7 @@ void worker_main(rlfc_server *srv)
                 }
                 size_t b = 0;
                 for (const Req &r : part)
-                    b += view_bytes(r.w, r.h);
+                    b += view_bytes(r.w, r.h, r.u8);
                 const uint32_t slot = srv->free_slots.back();
                 srv->free_slots.pop_back();
                 srv->in_use += b;
@@ -295,15 +302,15 @@ RLFC_API int rlfc_server_add(rlfc_server *srv, const rlfc_stream *s, uint32_t *l
     return RLFC_OK;
 }
 
-RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
-                                uint32_t out_w, uint32_t out_h, float *host_out, uint64_t *ticket)
+static int server_submit(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp, uint32_t out_w,
+                         uint32_t out_h, void *host_out, uint32_t u8, uint64_t *ticket)
 {
     using namespace rlfc;
     if (!srv || !host_out || out_w == 0 || out_h == 0) {
         set_error("rlfc_server_submit: null argument or empty size");
         return RLFC_E_INVALID_ARG;
     }
-    if (out_w > 32768 || out_h > 32768 || view_bytes(out_w, out_h) > srv->cfg.memory_budget) {
+    if (out_w > 32768 || out_h > 32768 || view_bytes(out_w, out_h, u8) > srv->cfg.memory_budget) {
         set_error("rlfc_server_submit: view larger than the memory budget or the renderer's limit");
         return RLFC_E_RANGE;
     }
@@ -313,7 +320,7 @@ RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float
             set_error("rlfc_server_submit: unknown light field");
             return RLFC_E_INVALID_ARG;
         }
-        Req r{srv->next_ticket++, lf_id, u, v, disp, out_w, out_h, host_out, now_s()};
+        Req r{srv->next_ticket++, lf_id, u, v, disp, out_w, out_h, u8, host_out, now_s()};
         srv->queue.push_back(r);
         srv->submitted++;
         if (ticket)
@@ -321,6 +328,18 @@ RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float
     }
     srv->cv.notify_all();
     return RLFC_OK;
+}
+
+RLFC_API int rlfc_server_submit(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
+                                uint32_t out_w, uint32_t out_h, float *host_out, uint64_t *ticket)
+{
+    return server_submit(srv, lf_id, u, v, disp, out_w, out_h, host_out, 0, ticket);
+}
+
+RLFC_API int rlfc_server_submit_u8(rlfc_server *srv, uint32_t lf_id, float u, float v, float disp,
+                                   uint32_t out_w, uint32_t out_h, uint8_t *host_out, uint64_t *ticket)
+{
+    return server_submit(srv, lf_id, u, v, disp, out_w, out_h, host_out, 1, ticket);
 }
 
 RLFC_API int rlfc_server_poll(rlfc_server *srv, rlfc_completion *out, size_t cap, size_t *n, int wait)

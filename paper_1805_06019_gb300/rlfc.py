@@ -67,7 +67,7 @@ EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_dec
            "rlfc_free_host", "rlfc_strerror", "rlfc_last_error", "rlfc_trace_enable", "rlfc_trace_read",
            "rlfc_batch_create", "rlfc_batch_set_config", "rlfc_batch_get_config", "rlfc_batch_decode",
            "rlfc_batch_autotune", "rlfc_batch_free", "rlfc_server_create", "rlfc_server_add",
-           "rlfc_server_submit", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free",
+           "rlfc_server_submit", "rlfc_server_submit_u8", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free",
            "rlfc_ks_search", "rlfc_ks_compact", "rlfc_ks_features", "rlfc_mlp_loss_grad", "rlfc_mlp_adam",
            "rlfc_mlp_predict"]
 
@@ -117,6 +117,7 @@ def lib():
             L.rlfc_server_add.argtypes = [vp, vp, ctypes.POINTER(u32)]
             L.rlfc_server_submit.argtypes = [vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float, u32, u32, vp,
                                              ctypes.POINTER(ctypes.c_uint64)]
+            L.rlfc_server_submit_u8.argtypes = L.rlfc_server_submit.argtypes
             L.rlfc_server_poll.argtypes = [vp, ctypes.POINTER(Completion), sz, ctypes.POINTER(sz), ctypes.c_int]
             L.rlfc_server_now.argtypes = []
             L.rlfc_server_now.restype = ctypes.c_double
@@ -349,13 +350,15 @@ class Server:
         return lf.value
 
     def submit(self, lf: int, u: float, v: float, disp: float, out: torch.Tensor) -> int:
-        """Queue a view of out.shape [H, W, 3] (float32 host tensor, ideally
-        pinned); returns its ticket."""
-        if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.dim() != 3:
-            raise TypeError("out must be a contiguous float32 host tensor [H, W, 3]")
+        """Queue a view of out.shape [H, W, 3] (float32 host tensor, or uint8
+        for 8-bit RGB; ideally pinned); returns its ticket."""
+        if out.is_cuda or out.dtype not in (torch.float32, torch.uint8) or not out.is_contiguous() \
+                or out.dim() != 3:
+            raise TypeError("out must be a contiguous float32 or uint8 host tensor [H, W, 3]")
         t = ctypes.c_uint64()
-        _check(lib().rlfc_server_submit(self._h, int(lf), float(u), float(v), float(disp), out.shape[1],
-                                        out.shape[0], ctypes.c_void_p(out.data_ptr()), ctypes.byref(t)))
+        fn = lib().rlfc_server_submit_u8 if out.dtype == torch.uint8 else lib().rlfc_server_submit
+        _check(fn(self._h, int(lf), float(u), float(v), float(disp), out.shape[1], out.shape[0],
+                  ctypes.c_void_p(out.data_ptr()), ctypes.byref(t)))
         self._outs[t.value] = out          # keep the destination alive until completion
         return t.value
 

@@ -143,3 +143,29 @@ def test_admission_limits(fleet):
     for i, o in enumerate(outs):
         want = oracle.render_view(lfs[0][1], 5, 5, 0.3 * i, 0.4 * i, 0.6, 64, 48)
         assert np.abs(o.numpy() - want).max() <= 1e-3
+
+
+def test_8bit_and_float_requests_in_one_server(fleet):
+    # interleaved 8-bit and float requests (same light field, same size, so
+    # only the format keeps them apart); each 8-bit view equals the 8-bit
+    # render of the same camera alone, each float view the float render
+    rl, lfs = fleet
+    st, _, (U, V, W, H) = lfs[0]
+    rng = np.random.default_rng(35)
+    cams = [(float(rng.random() * (U - 1)), float(rng.random() * (V - 1)), float(rng.choice([0.0, 0.6, 1.4])))
+            for _ in range(64)]
+    fmts = [torch.uint8 if i % 3 else torch.float32 for i in range(len(cams))]
+    srv = rl.Server(n_streams=2, max_batch=16, memory_budget=1 << 26)
+    lf_id = srv.add(st)
+    outs = [torch.empty((H, W, 3), dtype=f).pin_memory() for f in fmts]
+    for (u, v, d), o in zip(cams, outs):
+        srv.submit(lf_id, u, v, d, o)
+    comps = srv.poll(wait=True)
+    srv.close()
+    assert len(comps) == len(cams) and all(c["status"] == 0 for c in comps)
+    uv = torch.tensor([[u, v] for u, v, _ in cams], dtype=torch.float32, device="cuda")
+    disp = torch.tensor([d for _, _, d in cams], dtype=torch.float32, device="cuda")
+    ref8 = st.render(uv, disp, W, H, u8=True).cpu()
+    ref32 = st.render(uv, disp, W, H).cpu()
+    for i, o in enumerate(outs):
+        assert torch.equal(o, ref8[i] if fmts[i] == torch.uint8 else ref32[i]), i
