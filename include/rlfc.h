@@ -110,8 +110,12 @@ typedef struct {
  * so that kernels never read past a record.  The copy is done on
  * `cuda_stream` and the call returns after it completes, so host_bytes may be
  * freed right away.  *out receives a handle to release with rlfc_free_stream.
- * Errors: RLFC_E_INVALID_ARG, RLFC_E_FORMAT, RLFC_E_UNSUPPORTED, RLFC_E_OOM,
- * RLFC_E_CUDA.
+ * Errors: RLFC_E_INVALID_ARG, RLFC_E_FORMAT, RLFC_E_OOM, RLFC_E_CUDA, and
+ * RLFC_E_UNSUPPORTED for blocks other than 4 x 4 or when the largest |top
+ * value| plus (L - 1) times the largest |block value| exceeds 5460 (the
+ * kernels hold reconstructions in 16 bits; streams encoded from 8-bit views
+ * stay far below).  The block bound comes from the headers, or, where that
+ * bound is too loose, from decoding every block once on the device.
  */
 RLFC_API int rlfc_load_stream(const void *host_bytes, size_t nbytes, void *cuda_stream,
                      rlfc_stream **out);

@@ -40,13 +40,23 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kLeafMax = 64;      // views per leaf batch at most
 constexpr int kResCap = 384;      // stored leaf blocks decoded per batch at most
+constexpr uint32_t kZeroSlot = kResCap;   // a slot of zero residuals, for absent blocks
 constexpr int kRecs = 3 * kStrip;
-constexpr int kRowsPerJob = 32 / kStrip;   // block rows a warp converts per step (lane = row, location)
 constexpr int kLS = 56;                 // int16 per location in a node slab (48 used; 28 words keep
                                         // a half-warp's 8-byte reads on distinct banks)
 constexpr int kSlab = kStrip * kLS;     // int16 per node: [location][channel * 16 + value]
 constexpr uint32_t kSmemBudget = 200 * 1024;
 
+// Reconstructions and residuals are held as 16-bit values plus a bias of
+// 2^14, two to a word: then parent + residual is one 32-bit add for two
+// values (no carry crosses a half while every value stays in
+// [-2^14, 2^14)), and the inverse YCoCg-R runs on two pixels per
+// instruction.  The loader rejects streams whose values could leave that
+// range.
+constexpr uint32_t kB2 = 0x40004000u;     // the bias in both halves (a zero pair)
+constexpr uint32_t kHalfB2 = 0x20002000u;
+
+constexpr uint32_t kModeTable[kNumModes] = RLFC_MODE_TABLE_INIT;   // for the per-mode decoders
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
 
 struct Args {
@@ -67,21 +77,28 @@ struct Args {
 
 struct Smem {
     uint32_t *node;    // [S]
-    int16_t *top;      // [n_top][kSlab]
-    int16_t *inter;    // [n_int][kSlab]  internal reconstructions
-    int16_t *res;      // [kResCap][16]  decoded leaf blocks, one slot per listed block
-    uint16_t *map;     // [kLeafMax][kRecs]  slot of (leaf, record), 0xFFFF = not stored
+    int16_t *top;      // [n_top][kSlab]  biased
+    int16_t *inter;    // [n_int][kSlab]  internal reconstructions, biased
+    int16_t *res;      // [kResCap + 1][16]  decoded leaf blocks, biased; also the unsorted work list
+    uint16_t *map;     // [kLeafMax][kRecs]  slot of (leaf, record), kZeroSlot = not stored
     uint16_t *leafcnt; // [S - n_int]  stored blocks of each leaf over the strip
     uint32_t *mask;    // [kRecs][MW]
     uint32_t *mpre;    // [kRecs][MW]  stored blocks in front of each mask word
     void *off;         // [kRecs][pmax]  payload bit offset of each stored block (OffT)
-    uint2 *list;       // [list_cap]  (node | record << 16, rank)
+    uint2 *list;       // [list_cap]  (node | record << 16, rank | header << 14), sorted by mode
     uint32_t *stage;   // [stage_words]  the strip's records, from a 16-byte boundary
 };
 
 extern __shared__ __align__(16) unsigned char g_smem[];
 
 __host__ __device__ inline size_t r16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// The residual slots double as the unsorted work list.
+__host__ __device__ inline size_t res_bytes(uint32_t list_cap)
+{
+    const size_t a = 32ull * (kResCap + 1), b = 8ull * list_cap;
+    return r16(a > b ? a : b);
+}
 
 template <typename OffT>
 __device__ __forceinline__ Smem carve(const Args &a)
@@ -95,7 +112,7 @@ __device__ __forceinline__ Smem carve(const Args &a)
     m.inter = reinterpret_cast<int16_t *>(p);
     p += r16(2ull * a.n_int * kSlab);
     m.res = reinterpret_cast<int16_t *>(p);
-    p += r16(32ull * kResCap);
+    p += res_bytes(a.list_cap);
     m.map = reinterpret_cast<uint16_t *>(p);
     p += r16(2ull * kLeafMax * kRecs);
     m.leafcnt = reinterpret_cast<uint16_t *>(p);
@@ -115,10 +132,9 @@ __device__ __forceinline__ Smem carve(const Args &a)
 inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW, uint32_t pmax, uint32_t list_cap,
                          size_t off_size, uint32_t stage_words)
 {
-    return r16(4ull * S) + r16(2ull * n_top * kSlab) + r16(2ull * n_int * kSlab) +
-           r16(32ull * kResCap) + r16(2ull * kLeafMax * kRecs) + r16(2ull * S) +
-           r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) + r16(off_size * kRecs * pmax) + r16(8ull * list_cap) +
-           4ull * stage_words;
+    return r16(4ull * S) + r16(2ull * n_top * kSlab) + r16(2ull * n_int * kSlab) + res_bytes(list_cap) +
+           r16(2ull * kLeafMax * kRecs) + r16(2ull * S) + r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) +
+           r16(off_size * kRecs * pmax) + r16(8ull * list_cap) + 4ull * stage_words;
 }
 
 // Where record r of the strip starts: rec_base + rec_off[r] (the staged copy
@@ -128,20 +144,121 @@ struct RecSrc {
     const uint32_t *off;   // [kRecs]
 };
 
-// Stored blocks of nodes [p0, p1) over the strip's records, compacted into the
-// work list: (node | record << 16, rank).  Returns the item count.
-__device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uint32_t p0, uint32_t p1,
-                                               uint32_t *s_count, bool use_mask)
+// ---- one BISE block in a mode known at compile time --------------------
+//
+// The payload's words are aligned to its first bit once; every digit group
+// and low-bit field then sits at a fixed position.  Digit groups are split by
+// table: s_digit[t] holds the base-3 digits of t (t < 256) at bits 2e, and
+// s_digit[256 + t] the base-5 digits of t (t < 128) at bits 3e.  The 16
+// values come out dequantised and biased, two to a word.
+template <uint32_t K>
+__device__ __forceinline__ void decode_block_k(const uint32_t *w, uint32_t sh, uint32_t scale, uint32_t base,
+                                               const uint16_t *s_digit, uint32_t out[8])
+{
+    constexpr uint32_t M = kModeTable[K];
+    constexpr uint32_t kind = M >> 12, b = (M >> 8) & 15u, bits = M & 255u;
+    constexpr uint32_t D = kind == 1 ? 26u : (kind == 2 ? 38u : 0u);   // digit bits in front of the low parts
+    constexpr uint32_t NA = (bits + 31u) / 32u;                        // aligned payload words
+    if constexpr (bits == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            out[j] = __byte_perm(base, base, 0x5410);
+    } else {
+        uint32_t A[NA + 1];
+        {
+            uint32_t raw[NA + 1];
+#pragma unroll
+            for (uint32_t i = 0; i <= NA; i++)
+                raw[i] = w[i];
+#pragma unroll
+            for (uint32_t i = 0; i < NA; i++)
+                A[i] = __funnelshift_r(raw[i], raw[i + 1], sh);
+            A[NA] = 0u;
+        }
+        // bits [P, P + Wd) of the aligned payload (P, Wd constant after unrolling)
+        auto field = [&](uint32_t P, uint32_t Wd) -> uint32_t {
+            const uint32_t i = P >> 5, s = P & 31u;
+            const uint32_t mask = (1u << Wd) - 1u;
+            return (s + Wd <= 32u ? (A[i] >> s) : __funnelshift_r(A[i], A[i + 1], s)) & mask;
+        };
+        uint32_t dg[6];
+        if constexpr (kind == 1) {
+#pragma unroll
+            for (uint32_t g = 0; g < 3; g++)
+                dg[g] = s_digit[field(8u * g, 8u)];
+            const uint32_t t = field(24u, 2u);
+            dg[3] = t == 3u ? 0u : t;
+        } else if constexpr (kind == 2) {
+#pragma unroll
+            for (uint32_t g = 0; g < 5; g++)
+                dg[g] = s_digit[256u + field(7u * g, 7u)];
+            const uint32_t t = field(35u, 3u);
+            dg[5] = t >= 5u ? t - 5u : t;
+        }
+        uint32_t u[kVals];
+#pragma unroll
+        for (uint32_t v = 0; v < (uint32_t)kVals; v++) {
+            uint32_t digit = 0;
+            if constexpr (kind == 1)
+                digit = v == 15u ? dg[3] : (dg[v / 5u] >> (2u * (v % 5u))) & 3u;
+            else if constexpr (kind == 2)
+                digit = v == 15u ? dg[5] : (dg[v / 3u] >> (3u * (v % 3u))) & 7u;
+            uint32_t low = 0;
+            if constexpr (b > 0)
+                low = field(D + v * b, b);
+            u[v] = (digit << b) + low;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            out[j] = __byte_perm(u[2 * j] * scale + base, u[2 * j + 1] * scale + base, 0x5410);
+    }
+}
+
+__device__ __forceinline__ void decode_block(uint32_t mode, const uint32_t *w, uint32_t sh, uint32_t scale,
+                                          uint32_t base, const uint16_t *s_digit, uint32_t out[8])
+{
+    switch (mode) {
+#define RLFC_DECODE_CASE(K)                                   \
+    case K:                                                   \
+        decode_block_k<K>(w, sh, scale, base, s_digit, out);  \
+        break;
+        RLFC_DECODE_CASE(0) RLFC_DECODE_CASE(1) RLFC_DECODE_CASE(2) RLFC_DECODE_CASE(3)
+        RLFC_DECODE_CASE(4) RLFC_DECODE_CASE(5) RLFC_DECODE_CASE(6) RLFC_DECODE_CASE(7)
+        RLFC_DECODE_CASE(8) RLFC_DECODE_CASE(9) RLFC_DECODE_CASE(10) RLFC_DECODE_CASE(11)
+        RLFC_DECODE_CASE(12) RLFC_DECODE_CASE(13) RLFC_DECODE_CASE(14) RLFC_DECODE_CASE(15)
+        RLFC_DECODE_CASE(16) RLFC_DECODE_CASE(17) RLFC_DECODE_CASE(18) RLFC_DECODE_CASE(19)
+        RLFC_DECODE_CASE(20) RLFC_DECODE_CASE(21) RLFC_DECODE_CASE(22) RLFC_DECODE_CASE(23)
+        RLFC_DECODE_CASE(24) RLFC_DECODE_CASE(25) RLFC_DECODE_CASE(26) RLFC_DECODE_CASE(27)
+#undef RLFC_DECODE_CASE
+    default:   // modes >= 28 never pass the loader
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            out[j] = kB2;
+    }
+}
+
+// Stored blocks of nodes [p0, p1) over the strip's records, sorted by BISE
+// mode into m.list (so that a warp decodes blocks of one mode together):
+// item (node | record << 16, rank | header << 14).  With `leaf`, map[(p - p0)
+// * kRecs + r] receives the item's list position (its decode slot) or
+// kZeroSlot.  Returns the item count.
+__device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, const RecSrc &rs, uint32_t p0,
+                                                 uint32_t p1, bool use_mask, bool leaf, uint32_t *s_hist,
+                                                 uint32_t *s_count)
 {
     const int tid = threadIdx.x, lane = tid & 31;
+    uint2 *tmp = reinterpret_cast<uint2 *>(m.res);
+    if (tid < 32)
+        s_hist[tid] = 0;
     if (tid == 0)
         *s_count = 0;
     __syncthreads();
+    const uint32_t hdr0 = 32 * a.MW;
     const uint32_t pairs = (p1 - p0) * kRecs;
     for (uint32_t i0 = 0; i0 < pairs; i0 += kThreads) {
         const uint32_t i = i0 + tid;
         bool present = false;
-        uint32_t p = 0, r = 0, rank = 0;
+        uint32_t p = 0, r = 0, rank = 0, hdr = 0;
         if (i < pairs) {
             p = p0 + i / kRecs;
             r = i % kRecs;
@@ -149,121 +266,115 @@ __device__ __forceinline__ uint32_t build_list(const Args &a, const Smem &m, uin
             present = (word >> (p & 31u)) & 1u;
             if (present && use_mask)
                 present = a.needed[node_view(m.node[p])] != 0;
-            if (present)
+            if (present) {
                 rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
+                hdr = get_bits(rs.base + rs.off[r], hdr0 + kHdrBits * rank, kHdrBits);
+            }
+            if (leaf && !present)
+                m.map[i] = (uint16_t)kZeroSlot;
         }
         const unsigned bal = __ballot_sync(kFullMask, present);
-        uint32_t base = 0;
+        uint32_t at = 0;
         if (lane == 0 && bal)
-            base = atomicAdd(s_count, (uint32_t)__popc(bal));
-        base = __shfl_sync(kFullMask, base, 0);
-        if (present)
-            m.list[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(p | (r << 16), rank);
+            at = atomicAdd(s_count, (uint32_t)__popc(bal));
+        at = __shfl_sync(kFullMask, at, 0) + __popc(bal & ((1u << lane) - 1u));
+        const uint32_t mode = present ? hdr & 31u : 32u;
+        const unsigned peers = __match_any_sync(kFullMask, mode);
+        if (present) {
+            tmp[at] = make_uint2(p | (r << 16), rank | (hdr << 14));
+            if (lane == __ffs(peers) - 1)
+                atomicAdd(&s_hist[mode], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
-    return *s_count;
+    if (tid < 32) {
+        const uint32_t h = s_hist[tid];
+        s_hist[tid] = warp_inclusive_scan(h, lane) - h;   // first position of each mode
+    }
+    __syncthreads();
+    const uint32_t count = *s_count;
+    for (uint32_t i0 = 0; i0 < count; i0 += kThreads) {
+        const uint32_t i = i0 + tid;
+        uint2 it = make_uint2(0u, 0u);
+        if (i < count)
+            it = tmp[i];
+        const uint32_t mode = i < count ? (it.y >> 14) & 31u : 32u;
+        const unsigned peers = __match_any_sync(kFullMask, mode);
+        const int leader = __ffs(peers) - 1;
+        uint32_t at = 0;
+        if (i < count && lane == leader)
+            at = atomicAdd(&s_hist[mode], (uint32_t)__popc(peers));
+        at = __shfl_sync(kFullMask, at, leader) + __popc(peers & ((1u << lane) - 1u));
+        if (i < count) {
+            m.list[at] = it;
+            if (leaf) {
+                const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16;
+                m.map[(p - p0) * kRecs + r] = (uint16_t)at;
+            }
+        }
+    }
+    __syncthreads();
+    return count;
 }
 
-// One listed block, one thread: the residual (min + u) * 2^(q + shift) of its
-// 16 values, read with the sequential bit reader.
+// Decode the sorted list: internal blocks into their node's slab at
+// (node, location, channel), leaf blocks into slot = list position.
 template <typename OffT>
-__device__ __forceinline__ void decode_item(const Args &a, const Smem &m, const uint32_t *s_mode, uint2 it,
-                                            const RecSrc &rs, int32_t val[kVals])
+__device__ __forceinline__ void decode_sorted(const Args &a, const Smem &m, const uint16_t *s_digit, uint32_t count,
+                                              const RecSrc &rs, bool leaf)
 {
     const OffT *off = reinterpret_cast<const OffT *>(m.off);
-    const uint32_t rank = it.y, r = it.x >> 16;
-    const uint32_t *rec = rs.base + rs.off[r];
-    const BlockHeader h = unpack_header(get_bits(rec, 32 * a.MW + kHdrBits * rank, kHdrBits));
-    int32_t u[kVals];
-    bise_decode16(rec, off[r * a.pmax + rank], s_mode[h.mode], u);
-    const int32_t scale = 1 << (a.q + h.shift);
-#pragma unroll
-    for (int v = 0; v < kVals; v++)
-        val[v] = (h.min + u[v]) * scale;
-}
-
-// Internal nodes: each listed block into its node's slab,
-// dst[(node - p0) * kSlab + location * kLS + channel * 16 + value].
-template <typename OffT>
-__device__ __forceinline__ void decode_list(const Args &a, const Smem &m, const uint32_t *s_mode, uint32_t count,
-                                            const RecSrc &rs, uint32_t p0, int16_t *dst)
-{
     for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
         const uint2 it = m.list[i];
-        int32_t val[kVals];
-        decode_item<OffT>(a, m, s_mode, it, rs, val);
-        const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16;
-        const uint32_t loc = r / 3, c = r - 3 * loc;
-        uint2 *d = reinterpret_cast<uint2 *>(dst + (p - p0) * kSlab + loc * kLS + c * 16);
-#pragma unroll
-        for (int v = 0; v < kVals; v += 4)
-            d[v >> 2] = make_uint2(((uint32_t)val[v] & 0xFFFFu) | ((uint32_t)val[v + 1] << 16),
-                                   ((uint32_t)val[v + 2] & 0xFFFFu) | ((uint32_t)val[v + 3] << 16));
-    }
-}
-
-// Leaves: listed block i into compact slot i (16 int16, two 16-byte stores).
-template <typename OffT>
-__device__ __forceinline__ void decode_leaf_list(const Args &a, const Smem &m, const uint32_t *s_mode,
-                                                 uint32_t count, const RecSrc &rs)
-{
-    for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
-        int32_t val[kVals];
-        decode_item<OffT>(a, m, s_mode, m.list[i], rs, val);
-        uint32_t w[8];
-#pragma unroll
-        for (int v = 0; v < kVals; v += 2)
-            w[v >> 1] = ((uint32_t)val[v] & 0xFFFFu) | ((uint32_t)val[v + 1] << 16);
-        uint4 *d = reinterpret_cast<uint4 *>(m.res + (size_t)i * kVals);
-        d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    }
-}
-
-// Stored blocks of leaves [p0, p1) over the strip's records, compacted into
-// the work list (slot = list position); map[(p - p0) * kRecs + r] receives
-// the slot of (leaf p, record r) or 0xFFFF.  Returns the item count.
-__device__ __forceinline__ uint32_t build_leaf_list(const Args &a, const Smem &m, uint32_t p0, uint32_t p1,
-                                                    uint32_t *s_count, bool use_mask)
-{
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0)
-        *s_count = 0;
-    __syncthreads();
-    const uint32_t pairs = (p1 - p0) * kRecs;
-    for (uint32_t i0 = 0; i0 < pairs; i0 += kThreads) {
-        const uint32_t i = i0 + tid;
-        bool present = false;
-        uint32_t p = 0, r = 0, rank = 0;
-        if (i < pairs) {
-            p = p0 + i / kRecs;
-            r = i % kRecs;
-            const uint32_t word = m.mask[r * a.MW + (p >> 5)];
-            present = (word >> (p & 31u)) & 1u;
-            if (present && use_mask)
-                present = a.needed[node_view(m.node[p])] != 0;
-            if (present)
-                rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
+        const uint32_t r = it.x >> 16, rank = it.y & 0x3FFFu, hdr = it.y >> 14;
+        const uint32_t pos = off[r * a.pmax + rank];
+        const int32_t mn = ((int32_t)(hdr << 14)) >> 21;   // header bits 7..17, sign-extended
+        const uint32_t scale = 1u << (a.q + ((hdr >> 5) & 3u));
+        const uint32_t base = (uint32_t)mn * scale + 0x4000u;
+        uint32_t v[8];
+        decode_block(hdr & 31u, rs.base + rs.off[r] + (pos >> 5), pos & 31u, scale, base, s_digit, v);
+        int16_t *dst;
+        if (leaf) {
+            dst = m.res + (size_t)i * kVals;
+        } else {
+            const uint32_t p = it.x & 0xFFFFu, loc = r / 3, c = r - 3 * loc;
+            dst = m.inter + p * kSlab + loc * kLS + c * 16;
         }
-        const unsigned bal = __ballot_sync(kFullMask, present);
-        uint32_t base = 0;
-        if (lane == 0 && bal)
-            base = atomicAdd(s_count, (uint32_t)__popc(bal));
-        base = __shfl_sync(kFullMask, base, 0);
-        const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
-        if (present)
-            m.list[slot] = make_uint2(p | (r << 16), rank);
-        if (i < pairs)
-            m.map[i] = present ? (uint16_t)slot : (uint16_t)0xFFFFu;
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+        d[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        d[1] = make_uint4(v[4], v[5], v[6], v[7]);
     }
-    __syncthreads();
-    return *s_count;
+}
+
+__device__ __forceinline__ uint32_t clamp_biased_u8(uint32_t x)
+{
+    // each biased half into [2^14, 2^14 + 255]: its low byte is then the value
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(0x40004000u));
+    asm("min.u16x2 %0, %0, %1;" : "+r"(r) : "r"(0x40FF40FFu));
+    return r;
+}
+
+// Inverse YCoCg-R (Section 4) of two pixels held as biased halves; returns
+// R, G and B clamped to 8 bits in the low byte of each half.
+__device__ __forceinline__ void ycocg_pair_to_rgb(uint32_t y, uint32_t co, uint32_t cg, uint32_t &r, uint32_t &g,
+                                                  uint32_t &b)
+{
+    // (v + 2^14) >> 1 = floor(v / 2) + 2^13 in each half
+    const uint32_t hcg = (cg >> 1) & 0x7FFF7FFFu, hco = (co >> 1) & 0x7FFF7FFFu;
+    const uint32_t t = y - hcg + kHalfB2;   // y - floor(cg / 2)
+    g = clamp_biased_u8(cg + t - kB2);
+    const uint32_t bb = t - hco + kHalfB2;  // t - floor(co / 2)
+    r = clamp_biased_u8(bb + co - kB2);
+    b = clamp_biased_u8(bb);
 }
 
 template <bool kPacked, typename OffT>
 __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
 {
     __shared__ uint32_t s_mode[kNumModes];
+    __shared__ uint16_t s_digit[256 + 128];
+    __shared__ uint32_t s_hist[32];
     __shared__ uint32_t s_count;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bx0 = blockIdx.x * kStrip, by = blockIdx.y;
@@ -274,14 +385,32 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
 
     if (tid < kNumModes)
         s_mode[tid] = c_modes[tid];
+    for (uint32_t t = tid; t < 256 + 128; t += kThreads) {
+        // digits of t in base 3 (t < 256) or of t - 256 in base 5
+        const uint32_t base = t < 256 ? 3u : 5u, width = t < 256 ? 2u : 3u, n = t < 256 ? 5u : 3u;
+        uint32_t x = t < 256 ? t : t - 256, e = 0;
+        for (uint32_t k = 0; k < n; k++) {
+            e |= (x % base) << (width * k);
+            x /= base;
+        }
+        s_digit[t] = (uint16_t)e;
+    }
     for (uint32_t i = tid; i < a.S; i += kThreads)
         m.node[i] = a.node_info[i];
-    for (uint32_t i = tid; i < a.n_top * kStrip * 48; i += kThreads) {
-        const uint32_t t = i / (kStrip * 48), rest = i - t * kStrip * 48, loc = rest / 48, cv = rest - loc * 48;
-        m.top[t * kSlab + loc * kLS + cv] = loc < nl ? a.top[((size_t)t * a.nloc + b0 + loc) * 48 + cv] : 0;
+    {
+        // top RKV blocks, biased, two values per word
+        uint32_t *tw = reinterpret_cast<uint32_t *>(m.top);
+        const uint32_t *tg = reinterpret_cast<const uint32_t *>(a.top);
+        for (uint32_t i = tid; i < a.n_top * kStrip * 24; i += kThreads) {
+            const uint32_t t = i / (kStrip * 24), rest = i - t * (kStrip * 24), loc = rest / 24, wi = rest - loc * 24;
+            tw[t * (kSlab / 2) + loc * (kLS / 2) + wi] =
+                loc < nl ? (tg[((size_t)t * a.nloc + b0 + loc) * 24 + wi] ^ 0x80008000u) - kB2 : kB2;
+        }
     }
     for (uint32_t i = tid; i < a.n_int * kSlab / 2; i += kThreads)
-        reinterpret_cast<uint32_t *>(m.inter)[i] = 0;
+        reinterpret_cast<uint32_t *>(m.inter)[i] = kB2;
+    for (uint32_t i = tid; i < kVals / 2; i += kThreads)
+        reinterpret_cast<uint32_t *>(m.res + kZeroSlot * kVals)[i] = kB2;
     // the strip's records are contiguous in the stream: stage them (from a
     // 16-byte boundary, plus the two words the bit reader may read past a
     // record; the stream ends in zero padding) when they fit
@@ -334,42 +463,31 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
     }
     __syncthreads();
 
-    // ---- phase 2: internal nodes, decoded, then reconstructed level by level
-    if (a.n_int > 0) {
-        const uint32_t cnt = build_list(a, m, 0, a.n_int, &s_count, false);
-        decode_list<OffT>(a, m, s_mode, cnt, rs, 0, m.inter);
-        __syncthreads();
-        for (uint32_t p0 = 0; p0 < a.n_int;) {
-            const uint32_t lvl = node_level(m.node[p0]);
-            uint32_t p1 = p0;
-            while (p1 < a.n_int && node_level(m.node[p1]) == lvl)
-                p1++;
-            const bool from_top = lvl + 2 == a.L;
-            for (uint32_t i = tid; i < (p1 - p0) * kSlab; i += kThreads) {
-                const uint32_t p = p0 + i / kSlab, rest = i % kSlab;
-                const uint32_t par = node_parent(m.node[p]);
-                const int16_t *src = from_top ? m.top : m.inter;
-                m.inter[p * kSlab + rest] += src[par * kSlab + rest];
-            }
-            __syncthreads();
-            p0 = p1;
+    // ---- phases 2 and 3 share one loop (one copy of the list builder and of
+    // the per-mode decoders): the first pass takes the internal nodes
+    // (levels >= 1, first in BFS order), decodes them into their slabs and
+    // reconstructs them level by level; every later pass takes a batch of up
+    // to kLeafMax views whose stored blocks fit the kResCap decode slots
+    const bool use_mask = kPacked && a.needed != nullptr;
+    __shared__ uint32_t s_p1;
+    bool internal = a.n_int > 0;
+    if (!internal) {
+        for (uint32_t i = tid; i < kVals / 2; i += kThreads)
+            reinterpret_cast<uint32_t *>(m.res + kZeroSlot * kVals)[i] = kB2;
+        for (uint32_t p = tid; p < a.S; p += kThreads) {
+            uint32_t cnt = 0;
+            if (!use_mask || a.needed[node_view(m.node[p])])
+                for (uint32_t r = 0; r < kRecs; r++)
+                    cnt += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
+            m.leafcnt[p] = (uint16_t)cnt;
         }
     }
-
-    // ---- phase 3: the views, in batches of up to kLeafMax views whose stored
-    // blocks fit the kResCap decode slots
-    const bool use_mask = kPacked && a.needed != nullptr;
-    for (uint32_t p = a.n_int + tid; p < a.S; p += kThreads) {
-        uint32_t cnt = 0;
-        if (!use_mask || a.needed[node_view(m.node[p])])
-            for (uint32_t r = 0; r < kRecs; r++)
-                cnt += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
-        m.leafcnt[p - a.n_int] = (uint16_t)cnt;
-    }
-    __shared__ uint32_t s_p1;
-    for (uint32_t p0 = a.n_int; p0 < a.S;) {
+    for (uint32_t p0 = internal ? 0u : a.n_int; p0 < a.S;) {
         __syncthreads();
-        if (warp == 0) {
+        if (internal) {
+            if (tid == 0)
+                s_p1 = a.n_int;
+        } else if (warp == 0) {
             // the longest run of views from p0 whose stored blocks fit
             uint32_t sum = 0, p1 = p0;
             const uint32_t lim = min(a.S, p0 + kLeafMax);
@@ -390,42 +508,77 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
         }
         __syncthreads();
         const uint32_t p1 = s_p1, nb = p1 - p0;
-        const uint32_t cnt = build_leaf_list(a, m, p0, p1, &s_count, use_mask);
-        decode_leaf_list<OffT>(a, m, s_mode, cnt, rs);
+        const uint32_t cnt = build_sorted(a, m, rs, p0, p1, use_mask && !internal, !internal, s_hist, &s_count);
+        decode_sorted<OffT>(a, m, s_digit, cnt, rs, !internal);
         __syncthreads();
-        // parent + residual -> RGB: one (view, kRowsPerJob block rows) per
-        // warp step, lane = (row, location), four pixels per lane written
-        // straight to the output row
-        constexpr uint32_t kJobsPerView = 4 / kRowsPerJob;
-        for (uint32_t job = warp; job < nb * kJobsPerView; job += kWarps) {
-            const uint32_t j = job / kJobsPerView;
+        if (internal) {
+            for (uint32_t q0 = 0; q0 < a.n_int;) {
+                const uint32_t lvl = node_level(m.node[q0]);
+                uint32_t q1 = q0;
+                while (q1 < a.n_int && node_level(m.node[q1]) == lvl)
+                    q1++;
+                const uint4 *src = reinterpret_cast<const uint4 *>(lvl + 2 == a.L ? m.top : m.inter);
+                uint4 *dst = reinterpret_cast<uint4 *>(m.inter);
+                constexpr uint32_t kQ = kSlab / 8;   // uint4 per node slab
+                for (uint32_t i = tid; i < (q1 - q0) * kQ; i += kThreads) {
+                    const uint32_t p = q0 + i / kQ, rest = i % kQ;
+                    const uint4 s4 = src[node_parent(m.node[p]) * kQ + rest];
+                    uint4 d4 = dst[p * kQ + rest];
+                    d4.x = d4.x + s4.x - kB2;
+                    d4.y = d4.y + s4.y - kB2;
+                    d4.z = d4.z + s4.z - kB2;
+                    d4.w = d4.w + s4.w - kB2;
+                    dst[p * kQ + rest] = d4;
+                }
+                __syncthreads();
+                q0 = q1;
+            }
+            // the unsorted list may have covered the zero slot
+            for (uint32_t i = tid; i < kVals / 2; i += kThreads)
+                reinterpret_cast<uint32_t *>(m.res + kZeroSlot * kVals)[i] = kB2;
+            for (uint32_t p = a.n_int + tid; p < a.S; p += kThreads) {
+                uint32_t c = 0;
+                if (!use_mask || a.needed[node_view(m.node[p])])
+                    for (uint32_t r = 0; r < kRecs; r++)
+                        c += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
+                m.leafcnt[p - a.n_int] = (uint16_t)c;
+            }
+            internal = false;
+            p0 = a.n_int;
+            continue;
+        }
+        // parent + residual -> RGB: one view per warp step, lane = (block
+        // row, location), four pixels per lane written straight to the
+        // output row
+        for (uint32_t j = warp; j < nb; j += kWarps) {
             const uint32_t info = m.node[p0 + j];
             const uint32_t view = node_view(info);
             if (use_mask && !a.needed[view])
                 continue;
-            const uint32_t row = (job % kJobsPerView) * kRowsPerJob + lane / kStrip, loc = lane % kStrip;
+            const uint32_t row = (uint32_t)lane / kStrip, loc = (uint32_t)lane % kStrip;
             const uint32_t y = by * 4 + row, x = (bx0 + loc) * 4;
             if (loc >= nl || y >= a.H)
                 continue;
-            const int16_t *base = (a.L == 2 ? m.top : m.inter) + node_parent(info) * kSlab + loc * kLS + row * 4;
-            int32_t ycc[3][4];
+            const int16_t *par = (a.L == 2 ? m.top : m.inter) + node_parent(info) * kSlab + loc * kLS + row * 4;
+            uint2 ycc[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const uint2 pb = *reinterpret_cast<const uint2 *>(base + c * 16);
+                const uint2 pb = *reinterpret_cast<const uint2 *>(par + c * 16);
                 const uint32_t slot = m.map[j * kRecs + loc * 3 + c];
-                const uint2 rb = slot != 0xFFFFu ? *reinterpret_cast<const uint2 *>(m.res + slot * kVals + row * 4)
-                                                 : make_uint2(0u, 0u);
-                ycc[c][0] = (int32_t)(int16_t)(pb.x & 0xFFFFu) + (int32_t)(int16_t)(rb.x & 0xFFFFu);
-                ycc[c][1] = (int32_t)(int16_t)(pb.x >> 16) + (int32_t)(int16_t)(rb.x >> 16);
-                ycc[c][2] = (int32_t)(int16_t)(pb.y & 0xFFFFu) + (int32_t)(int16_t)(rb.y & 0xFFFFu);
-                ycc[c][3] = (int32_t)(int16_t)(pb.y >> 16) + (int32_t)(int16_t)(rb.y >> 16);
+                const uint2 rb = *reinterpret_cast<const uint2 *>(m.res + slot * kVals + row * 4);
+                ycc[c] = make_uint2(pb.x + rb.x - kB2, pb.y + rb.y - kB2);
             }
-            uint32_t px[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                px[k] = ycocg_to_rgb24(ycc[0][k], ycc[1][k], ycc[2][k]);
+            uint32_t r01, g01, b01, r23, g23, b23;
+            ycocg_pair_to_rgb(ycc[0].x, ycc[1].x, ycc[2].x, r01, g01, b01);
+            ycocg_pair_to_rgb(ycc[0].y, ycc[1].y, ycc[2].y, r23, g23, b23);
+            const uint32_t t01 = __byte_perm(r01, g01, 0x6240);   // R0 G0 R1 G1
+            const uint32_t t23 = __byte_perm(r23, g23, 0x6240);   // R2 G2 R3 G3
             const bool whole = x + 4 <= a.W;
             if (kPacked) {
+                const uint32_t px[4] = {__byte_perm(t01, b01, 0x0410) & 0xFFFFFFu,
+                                        __byte_perm(t01, b01, 0x0632) & 0xFFFFFFu,
+                                        __byte_perm(t23, b23, 0x0410) & 0xFFFFFFu,
+                                        __byte_perm(t23, b23, 0x0632) & 0xFFFFFFu};
                 uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)view * a.H + y) * a.W + x;
                 if (whole && a.out_aligned16 && (a.W & 3u) == 0) {
                     *reinterpret_cast<uint4 *>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
@@ -434,20 +587,20 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
                         dst[k] = px[k];
                 }
             } else {
+                // 4 pixels = 12 bytes: R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
+                const uint32_t w0 = __byte_perm(t01, b01, 0x2410);
+                const uint32_t w1 = __byte_perm(__byte_perm(t01, b01, 0x0063), t23, 0x5410);
+                const uint32_t w2 = __byte_perm(b23, t23, 0x2760);
                 uint8_t *dst = a.out + (((size_t)view * a.H + y) * a.W + x) * 3;
                 if (whole && a.out_aligned4 && (a.W & 3u) == 0) {
-                    // 4 pixels = 12 bytes = 3 words at a 4-byte boundary, each
-                    // assembled by one byte permute of two neighbouring pixels
                     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-                    d[0] = __byte_perm(px[0], px[1], 0x4210);
-                    d[1] = __byte_perm(px[1], px[2], 0x5421);
-                    d[2] = __byte_perm(px[2], px[3], 0x6542);
+                    d[0] = w0;
+                    d[1] = w1;
+                    d[2] = w2;
                 } else {
-                    for (uint32_t k = 0; k < 4 && x + k < a.W; k++) {
-                        dst[3 * k] = (uint8_t)px[k];
-                        dst[3 * k + 1] = (uint8_t)(px[k] >> 8);
-                        dst[3 * k + 2] = (uint8_t)(px[k] >> 16);
-                    }
+                    const uint32_t wv[3] = {w0, w1, w2};
+                    for (uint32_t k = 0; k < 12 && x + k / 3 < a.W; k++)
+                        dst[k] = (uint8_t)(wv[k >> 2] >> (8 * (k & 3)));
                 }
             }
         }

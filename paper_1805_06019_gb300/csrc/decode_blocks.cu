@@ -68,7 +68,61 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) decode_blocks_kernel(const 
     }
 }
 
+// One thread per record: every stored block decoded, the largest
+// |(min + u) * 2^(q + shift)| over the record, reduced per warp into *out.
+__global__ void __launch_bounds__(256) block_magnitude_kernel(const uint32_t *records, const uint32_t *offsets,
+                                                              uint32_t n_rec, uint32_t MW, uint32_t q,
+                                                              uint32_t *out)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t mx = 0;
+    if (r < n_rec) {
+        const uint32_t *rec = records + offsets[r];
+        uint32_t P = 0;
+        for (uint32_t w = 0; w < MW; w++)
+            P += __popc(rec[w]);
+        const uint32_t hdr0 = 32 * MW;
+        uint32_t pos = hdr0 + kHdrBits * P;
+        for (uint32_t h = 0; h < P; h++) {
+            const BlockHeader hd = unpack_header(get_bits(rec, hdr0 + kHdrBits * h, kHdrBits));
+            const uint32_t mode = c_modes[hd.mode];
+            int32_t u[kVals];
+            bise_decode16(rec, pos, mode, u);
+            int32_t lo = u[0], hi = u[0];
+#pragma unroll
+            for (int v = 1; v < kVals; v++) {
+                lo = min(lo, u[v]);
+                hi = max(hi, u[v]);
+            }
+            const int32_t a = hd.min + lo, b = hd.min + hi;
+            mx = max(mx, (uint32_t)max(abs(a), abs(b)) << (q + hd.shift));
+            pos += mode_bits(mode);
+        }
+    }
+    mx = __reduce_max_sync(kFullMask, mx);
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, mx);
+}
+
 }  // namespace
+
+int block_magnitude(const rlfc_stream *s, cudaStream_t st, uint32_t *mag)
+{
+    const uint32_t n_rec = 3 * s->info.nloc_x * s->info.nloc_y;
+    uint32_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, 4, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "block magnitude: allocation");
+    if ((e = cudaMemsetAsync(d, 0, 4, st)) == cudaSuccess) {
+        { rlfc::TraceScope trace_("block_magnitude_kernel", st); block_magnitude_kernel<<<(n_rec + 255) / 256, 256, 0, st>>>(s->d_records, s->d_offsets, n_rec, s->MW, s->info.q, d); }
+        if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaMemcpyAsync(mag, d, 4, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(d, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "block magnitude");
+    return RLFC_OK;
+}
 
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc, uint32_t n,
                          uint8_t *d_out, uint8_t *d_status, cudaStream_t st)

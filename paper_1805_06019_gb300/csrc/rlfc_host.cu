@@ -44,6 +44,20 @@ uint32_t payload_bits16(uint32_t k)
     return 16u * (g + 1) + 26u;     // 3 * 2^(g+1)
 }
 
+// the range N of mode k (1 2 3 4 5 6 8 10 12 16 ... 768 1024)
+uint32_t range16(uint32_t k)
+{
+    if (k < 3)
+        return k + 1;
+    const uint32_t g = (k - 3) / 3, r = (k - 3) % 3;
+    return r == 0 ? 4u << g : (r == 1 ? 5u << g : 6u << g);
+}
+
+// Largest |Y|, |Co|, |Cg| the GPU kernels accept: they hold reconstructions
+// and the inverse YCoCg-R intermediates (up to 3M + 2) as 16-bit values with
+// a bias of 2^14.
+constexpr uint64_t kMaxMagnitude = 5460;
+
 }  // namespace
 
 // BFS numbering of the SRV nodes (Section 3.4): start from every top node in
@@ -114,6 +128,7 @@ struct Parsed {
     uint32_t U, V, W, H, B, L, q, n_top, S;
     uint64_t off_top, off_offsets, off_records, record_words;
     uint32_t Wp, Hp, nlx, nly, nloc, MW, max_record_words, max_strip_words, max_present;
+    uint64_t max_top_mag, max_block_mag;   // largest |top value| and bound on |block value|
     Tables tab;
 };
 
@@ -187,6 +202,12 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
     ps.MW = (ps.S + 31) / 32;
     ps.max_record_words = 0;
     ps.max_present = 0;
+    ps.max_block_mag = 0;
+    ps.max_top_mag = 0;
+    for (uint64_t i = 0; i < top_bytes / 2; i++) {
+        const int32_t v = (int16_t)(uint16_t)(p[ps.off_top + 2 * i] | (p[ps.off_top + 2 * i + 1] << 8));
+        ps.max_top_mag = std::max<uint64_t>(ps.max_top_mag, (uint64_t)(v < 0 ? -v : v));
+    }
     const uint8_t *off = p + ps.off_offsets;
     const uint8_t *rec = p + ps.off_records;
     if (rd32(off) != 0 || rd32(off + 4 * (noff - 1)) != ps.record_words)
@@ -219,10 +240,17 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
                 uint64_t win = rd32(rp + 4 * wi);
                 if (wi + 1 < words)
                     win |= (uint64_t)rd32(rp + 4 * (wi + 1)) << 32;
-                const uint32_t k = (uint32_t)(win >> (hp & 31)) & 31u;
+                const uint32_t hdr = (uint32_t)(win >> (hp & 31)) & 0x3FFFFu;
+                const uint32_t k = hdr & 31u;
                 if (k >= 28)
                     return fmt("block mode out of range");
                 bits += payload_bits16(k);
+                // |(min + u) * 2^(q + shift)| for u in [0, N)
+                const int64_t mn = ((int32_t)(hdr << 14)) >> 21;
+                const int64_t hi = mn + (int64_t)range16(k) - 1;
+                const uint64_t mag = (uint64_t)std::max(mn < 0 ? -mn : mn, hi < 0 ? -hi : hi)
+                                     << (ps.q + ((hdr >> 5) & 3u));
+                ps.max_block_mag = std::max(ps.max_block_mag, mag);
             }
             if ((bits + 31) / 32 != words)
                 return fmt("record length disagrees with its blocks");
@@ -238,6 +266,10 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
         }
     if (ps.B != 4) {
         set_error("the GPU kernels decode 4x4 blocks only");
+        return RLFC_E_UNSUPPORTED;
+    }
+    if (ps.max_top_mag > kMaxMagnitude) {
+        set_error("reconstructed values can leave the 16-bit range of the GPU kernels");
         return RLFC_E_UNSUPPORTED;
     }
     return RLFC_OK;
@@ -324,6 +356,20 @@ int load(const uint8_t *bytes, size_t nbytes, cudaStream_t st, rlfc_stream **out
         free_device(s);
         delete s;
         return cuda_fail(e, "uploading the stream");
+    }
+    // the headers bound every block value; where that bound is too loose for
+    // the 16-bit range, decode every block once and take the exact bound
+    if (ps.max_top_mag + (uint64_t)(ps.L - 1) * ps.max_block_mag > kMaxMagnitude) {
+        uint32_t mag = 0;
+        const int rc = block_magnitude(s, st, &mag);
+        if (rc != RLFC_OK || ps.max_top_mag + (uint64_t)(ps.L - 1) * mag > kMaxMagnitude) {
+            free_device(s);
+            delete s;
+            if (rc != RLFC_OK)
+                return rc;
+            set_error("reconstructed values can leave the 16-bit range of the GPU kernels");
+            return RLFC_E_UNSUPPORTED;
+        }
     }
     *out = s;
     return RLFC_OK;

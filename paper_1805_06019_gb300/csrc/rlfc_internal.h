@@ -91,6 +91,8 @@ int cuda_fail(cudaError_t e, const char *what);
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
 // every view the mask marks (all when null), as packed RGB words [view][H][W]
 int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, cudaStream_t st);
+// Largest |value| of any stored block of the stream, decoded (synchronous).
+int block_magnitude(const rlfc_stream *s, cudaStream_t st, uint32_t *mag);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
                          uint32_t n, uint8_t *d_out, uint8_t *d_status, cudaStream_t st);
 // d_out8: when set, 8-bit RGB output instead of d_out

@@ -104,3 +104,21 @@ def test_block_size_other_than_four_is_unsupported(lib):
     rc, _ = _load(lib, data)
     assert rc == E_UNSUPPORTED
     assert "4x4" in lib.rlfc_last_error().decode()
+
+
+def test_values_beyond_the_16_bit_range_are_unsupported(lib):
+    # a top value of 6000 exceeds the largest magnitude the kernels hold
+    # exactly (5460: the inverse YCoCg-R reaches 3M + 2 < 2^14); the same
+    # stream with an in-range value passes validation and fails only later,
+    # without a GPU, at the device copy
+    s = _stream()
+    off_top = int.from_bytes(s[44:48], "little")
+    big = bytearray(s); big[off_top:off_top + 2] = (6000).to_bytes(2, "little", signed=True)
+    rc, h = _load(lib, bytes(big))
+    assert rc == E_UNSUPPORTED and not h.value
+    assert "16-bit" in lib.rlfc_last_error().decode()
+    ok = bytearray(s); ok[off_top:off_top + 2] = (-300).to_bytes(2, "little", signed=True)
+    rc, h = _load(lib, bytes(ok))
+    assert rc not in (E_FORMAT, E_UNSUPPORTED), lib.rlfc_last_error()
+    if h.value:
+        lib.rlfc_free_stream(h)

@@ -310,3 +310,22 @@ def test_render_u8_output(rlfc, name, size):
         want = oracle.to_u8(oracle.render_view(lf, U, V, float(uv[r, 0]), float(uv[r, 1]), float(disp[r]),
                                                out_w, out_h)).astype(np.int32)
         assert np.abs(b[r].astype(np.int32) - want).max() <= 1
+
+
+def test_streams_beyond_the_16_bit_range_are_refused_on_load(rlfc):
+    rl = rlfc
+    # the first stored block's header patched to min -1024 and shift 3: its
+    # decoded values reach 8192 in magnitude, beyond what the kernels hold in
+    # 16 bits; the header bound fails, the decoded check confirms it
+    rng = np.random.default_rng(0)
+    lf = rng.integers(0, 256, size=(9, 12, 16, 3), dtype=np.uint8)
+    s = bytearray(oracle.encode(lf, 3, 3, B=4, L=2, c=[0, 3], tau_p=3, tau_b=20))
+    off_records = int.from_bytes(s[52:56], "little")
+    assert int.from_bytes(s[off_records:off_records + 4], "little") != 0   # S = 9: one mask word
+    w = int.from_bytes(s[off_records + 4:off_records + 8], "little")
+    hdr = (w & 31) | (3 << 5) | (0x400 << 7)
+    s[off_records + 4:off_records + 8] = ((w & ~0x3FFFF) | hdr).to_bytes(4, "little")
+    assert oracle.Stream(bytes(s)).decode_all() is not None      # a valid stream for the oracle
+    with pytest.raises(rl.RLFCError) as ei:
+        rl.Stream(bytes(s))
+    assert ei.value.code == 3 and "16-bit" in str(ei.value)
