@@ -612,7 +612,8 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         const float b1[3] = {rg1.x, rg1.y, __low2float(*reinterpret_cast<const __half2 *>(&p1.y))};
 #pragma unroll
                         for (int ch = 0; ch < 3; ch++) {
-                            acc[rr][ch] += w00 * a0[ch] + w10 * a1[ch] + w01 * b0[ch] + w11 * b1[ch];
+                            // one FMA per tap, in the order 00, 10, 01, 11
+                            acc[rr][ch] = fmaf(w11, b1[ch], fmaf(w01, b0[ch], fmaf(w10, a1[ch], fmaf(w00, a0[ch], acc[rr][ch]))));
                             a0[ch] = b0[ch];
                             a1[ch] = b1[ch];
                         }
