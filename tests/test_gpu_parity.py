@@ -329,3 +329,48 @@ def test_streams_beyond_the_16_bit_range_are_refused_on_load(rlfc):
     with pytest.raises(rl.RLFCError) as ei:
         rl.Stream(bytes(s))
     assert ei.value.code == 3 and "16-bit" in str(ei.value)
+
+
+def _modes_of(data: bytes) -> set:
+    """BISE modes of every stored block of a stream (format v1: header at 0,
+    offsets and records at the offsets the header gives)."""
+    rd = lambda o: int.from_bytes(data[o:o + 4], "little")
+    W, H, S = rd(16), rd(20), rd(40)
+    off_offsets, off_records, rw = rd(48), rd(52), rd(56)
+    MW = (S + 31) // 32
+    nloc = ((W + 3) // 4) * ((H + 3) // 4)
+    words = np.frombuffer(data[off_records:off_records + 4 * rw], dtype=np.uint32)
+    offs = np.frombuffer(data[off_offsets:off_offsets + 4 * (3 * nloc + 1)], dtype=np.uint32)
+    modes = set()
+    for r in range(3 * nloc):
+        rec = words[offs[r]:offs[r + 1]]
+        bits = np.unpackbits(rec.view(np.uint8), bitorder="little")
+        P = int(bits[:32 * MW].sum())
+        for h in range(P):
+            pos = 32 * MW + 18 * h
+            modes.add(int(sum(int(bits[pos + i]) << i for i in range(5))))
+    return modes
+
+
+def test_every_bise_mode_decodes_bit_exactly(rlfc):
+    # the per-mode block decoders: a stream whose level-0 modes are forced at
+    # random (every feasible range from 2 up to 1024, shifts 0..3) and a
+    # stream whose views are half flat (constant residual blocks, range 1)
+    # and half textured; together they hold all 28 modes
+    U, V, W, H = 5, 5, 40, 24
+    lf = lf_synth.make_lightfield(U, V, W, H, [0.0, 0.8, 1.7], 1.0, preset_id=800)
+    nloc = ((W + 3) // 4) * ((H + 3) // 4)
+    rng = np.random.default_rng(0)
+    modes = rng.integers(0, 128, U * V * 3 * nloc).astype(np.uint8)
+    modes[rng.random(modes.size) < 0.2] = 0xFF
+    forced = oracle.encode(lf, U, V, B=4, L=3, c=[0, 2, 3], tau_p=2, tau_b=32, mode_space=1, tau_err=4,
+                           lam_q8=256, leaf_modes=modes)
+    half = lf.copy()
+    half[:, :, : W // 2] = ((np.arange(U * V) * 7 % 200 + 20).astype(np.uint8))[:, None, None, None]
+    mixed = oracle.encode(half, U, V, B=4, L=3, c=[0, 2, 3], tau_p=1, tau_b=8)
+    seen = set()
+    for data in (forced, mixed):
+        seen |= _modes_of(data)
+        got = rlfc.Stream(data).decode_all().cpu().numpy()
+        assert np.array_equal(got, oracle.Stream(data).decode_all())
+    assert seen == set(range(28)), sorted(set(range(28)) - seen)
