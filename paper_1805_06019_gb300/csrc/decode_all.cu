@@ -81,7 +81,8 @@ struct Smem {
     int16_t *inter;    // [n_int][kSlab]  internal reconstructions, biased
     int16_t *res;      // [kResCap + 1][16]  decoded leaf blocks, biased; also the unsorted work list
     uint16_t *map;     // [kLeafMax][kRecs]  slot of (leaf, record), kZeroSlot = not stored
-    uint16_t *leafcnt; // [S - n_int]  stored blocks of each leaf over the strip
+    uint16_t *leafcnt; // [S - n_int]  stored blocks of each leaf (in batch order) over the strip
+    uint16_t *leaves;  // [S - n_int]  with a view mask: the needed leaves, the order batches take
     uint32_t *mask;    // [kRecs][MW]
     uint32_t *mpre;    // [kRecs][MW]  stored blocks in front of each mask word
     void *off;         // [kRecs][pmax]  payload bit offset of each stored block (OffT)
@@ -117,6 +118,8 @@ __device__ __forceinline__ Smem carve(const Args &a)
     p += r16(2ull * kLeafMax * kRecs);
     m.leafcnt = reinterpret_cast<uint16_t *>(p);
     p += r16(2ull * a.S);
+    m.leaves = reinterpret_cast<uint16_t *>(p);
+    p += r16(2ull * a.S);
     m.mask = reinterpret_cast<uint32_t *>(p);
     p += r16(4ull * kRecs * a.MW);
     m.mpre = reinterpret_cast<uint32_t *>(p);
@@ -133,7 +136,7 @@ inline size_t smem_bytes(uint32_t S, uint32_t n_top, uint32_t n_int, uint32_t MW
                          size_t off_size, uint32_t stage_words)
 {
     return r16(4ull * S) + r16(2ull * n_top * kSlab) + r16(2ull * n_int * kSlab) + res_bytes(list_cap) +
-           r16(2ull * kLeafMax * kRecs) + r16(2ull * S) + r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) +
+           r16(2ull * kLeafMax * kRecs) + 2 * r16(2ull * S) + r16(4ull * kRecs * MW) + r16(4ull * kRecs * MW) +
            r16(off_size * kRecs * pmax) + r16(8ull * list_cap) + 4ull * stage_words;
 }
 
@@ -237,14 +240,15 @@ __device__ __forceinline__ void decode_block(uint32_t mode, const uint32_t *w, u
     }
 }
 
-// Stored blocks of nodes [p0, p1) over the strip's records, sorted by BISE
-// mode into m.list (so that a warp decodes blocks of one mode together):
-// item (node | record << 16, rank | header << 14).  With `leaf`, map[(p - p0)
-// * kRecs + r] receives the item's list position (its decode slot) or
-// kZeroSlot.  Returns the item count.
-__device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, const RecSrc &rs, uint32_t p0,
-                                                 uint32_t p1, bool use_mask, bool leaf, uint32_t *s_hist,
-                                                 uint32_t *s_count)
+// Stored blocks of the nodes at positions [q0, q1) of a node sequence
+// (seq[q], or base + q without a list) over the strip's records, sorted by
+// BISE mode into m.list (so that a warp decodes blocks of one mode
+// together): item (j | record << 16, rank | header << 14), j = q - q0.  With
+// `leaf`, map[j * kRecs + r] receives the item's list position (its decode
+// slot) or kZeroSlot.  Returns the item count.
+__device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, const RecSrc &rs, uint32_t q0,
+                                                 uint32_t q1, const uint16_t *seq, uint32_t base, bool leaf,
+                                                 uint32_t *s_hist, uint32_t *s_count)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     uint2 *tmp = reinterpret_cast<uint2 *>(m.res);
@@ -254,18 +258,17 @@ __device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, c
         *s_count = 0;
     __syncthreads();
     const uint32_t hdr0 = 32 * a.MW;
-    const uint32_t pairs = (p1 - p0) * kRecs;
+    const uint32_t pairs = (q1 - q0) * kRecs;
     for (uint32_t i0 = 0; i0 < pairs; i0 += kThreads) {
         const uint32_t i = i0 + tid;
         bool present = false;
-        uint32_t p = 0, r = 0, rank = 0, hdr = 0;
+        uint32_t j = 0, r = 0, rank = 0, hdr = 0;
         if (i < pairs) {
-            p = p0 + i / kRecs;
+            j = i / kRecs;
             r = i % kRecs;
+            const uint32_t p = seq ? seq[q0 + j] : base + q0 + j;
             const uint32_t word = m.mask[r * a.MW + (p >> 5)];
             present = (word >> (p & 31u)) & 1u;
-            if (present && use_mask)
-                present = a.needed[node_view(m.node[p])] != 0;
             if (present) {
                 rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
                 hdr = get_bits(rs.base + rs.off[r], hdr0 + kHdrBits * rank, kHdrBits);
@@ -281,7 +284,7 @@ __device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, c
         const uint32_t mode = present ? hdr & 31u : 32u;
         const unsigned peers = __match_any_sync(kFullMask, mode);
         if (present) {
-            tmp[at] = make_uint2(p | (r << 16), rank | (hdr << 14));
+            tmp[at] = make_uint2(j | (r << 16), rank | (hdr << 14));
             if (lane == __ffs(peers) - 1)
                 atomicAdd(&s_hist[mode], (uint32_t)__popc(peers));
         }
@@ -307,10 +310,8 @@ __device__ __forceinline__ uint32_t build_sorted(const Args &a, const Smem &m, c
         at = __shfl_sync(kFullMask, at, leader) + __popc(peers & ((1u << lane) - 1u));
         if (i < count) {
             m.list[at] = it;
-            if (leaf) {
-                const uint32_t p = it.x & 0xFFFFu, r = it.x >> 16;
-                m.map[(p - p0) * kRecs + r] = (uint16_t)at;
-            }
+            if (leaf)
+                m.map[(it.x & 0xFFFFu) * kRecs + (it.x >> 16)] = (uint16_t)at;
         }
     }
     __syncthreads();
@@ -337,7 +338,7 @@ __device__ __forceinline__ void decode_sorted(const Args &a, const Smem &m, cons
         if (leaf) {
             dst = m.res + (size_t)i * kVals;
         } else {
-            const uint32_t p = it.x & 0xFFFFu, loc = r / 3, c = r - 3 * loc;
+            const uint32_t p = it.x & 0xFFFFu, loc = r / 3, c = r - 3 * loc;   // internal pass: j = node
             dst = m.inter + p * kSlab + loc * kLS + c * 16;
         }
         uint4 *d = reinterpret_cast<uint4 *>(dst);
@@ -469,59 +470,88 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
     // reconstructs them level by level; every later pass takes a batch of up
     // to kLeafMax views whose stored blocks fit the kResCap decode slots
     const bool use_mask = kPacked && a.needed != nullptr;
-    __shared__ uint32_t s_p1;
-    bool internal = a.n_int > 0;
-    if (!internal) {
+    __shared__ uint32_t s_p1, s_nleaf;
+    // the leaf sequence the batches take: every leaf in BFS order, or, with a
+    // view mask, only the needed leaves (compacted)
+    if (use_mask) {
+        if (tid == 0)
+            s_nleaf = 0;
+        __syncthreads();
+        for (uint32_t b = a.n_int; b < a.S; b += kThreads) {
+            const uint32_t p = b + tid;
+            const bool need = p < a.S && a.needed[node_view(m.node[p])] != 0;
+            const unsigned bal = __ballot_sync(kFullMask, need);
+            uint32_t at = 0;
+            if (lane == 0 && bal)
+                at = atomicAdd(&s_nleaf, (uint32_t)__popc(bal));
+            at = __shfl_sync(kFullMask, at, 0) + __popc(bal & ((1u << lane) - 1u));
+            if (need)
+                m.leaves[at] = (uint16_t)p;
+        }
+        __syncthreads();
+    }
+    const uint32_t nleaf = use_mask ? s_nleaf : a.S - a.n_int;
+    const uint16_t *seq = use_mask ? m.leaves : nullptr;
+    auto leaf_node = [&](uint32_t q) -> uint32_t { return use_mask ? (uint32_t)m.leaves[q] : a.n_int + q; };
+    // stored blocks of each leaf of the sequence over the strip, and the
+    // zero slot (which the internal pass's unsorted list may have covered)
+    auto prepare_leaves = [&]() {
         for (uint32_t i = tid; i < kVals / 2; i += kThreads)
             reinterpret_cast<uint32_t *>(m.res + kZeroSlot * kVals)[i] = kB2;
-        for (uint32_t p = tid; p < a.S; p += kThreads) {
-            uint32_t cnt = 0;
-            if (!use_mask || a.needed[node_view(m.node[p])])
-                for (uint32_t r = 0; r < kRecs; r++)
-                    cnt += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
-            m.leafcnt[p] = (uint16_t)cnt;
+        for (uint32_t q = tid; q < nleaf; q += kThreads) {
+            const uint32_t p = leaf_node(q);
+            uint32_t c = 0;
+            for (uint32_t r = 0; r < kRecs; r++)
+                c += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
+            m.leafcnt[q] = (uint16_t)c;
         }
-    }
-    for (uint32_t p0 = internal ? 0u : a.n_int; p0 < a.S;) {
+    };
+    bool internal = a.n_int > 0;
+    if (!internal)
+        prepare_leaves();
+    for (uint32_t q0 = 0; internal || q0 < nleaf;) {
         __syncthreads();
         if (internal) {
             if (tid == 0)
                 s_p1 = a.n_int;
         } else if (warp == 0) {
-            // the longest run of views from p0 whose stored blocks fit
-            uint32_t sum = 0, p1 = p0;
-            const uint32_t lim = min(a.S, p0 + kLeafMax);
-            for (uint32_t q0 = p0; q0 < lim; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                const uint32_t c = q < lim ? m.leafcnt[q - a.n_int] : (uint32_t)kResCap + 1;
+            // the longest run of sequence positions from q0 whose stored blocks fit
+            uint32_t sum = 0, q1 = q0;
+            const uint32_t lim = min(nleaf, q0 + kLeafMax);
+            for (uint32_t b = q0; b < lim; b += 32) {
+                const uint32_t q = b + lane;
+                const uint32_t c = q < lim ? m.leafcnt[q] : (uint32_t)kResCap + 1;
                 const uint32_t incl = warp_inclusive_scan(c, lane);
                 const unsigned ok = __ballot_sync(kFullMask, sum + incl <= (uint32_t)kResCap);
                 const uint32_t n_ok = __popc(ok);
                 if (n_ok)
                     sum += __shfl_sync(kFullMask, incl, n_ok - 1);
-                p1 = q0 + n_ok;
+                q1 = b + n_ok;
                 if (n_ok < 32)
                     break;
             }
             if (lane == 0)
-                s_p1 = max(p1, p0 + 1);
+                s_p1 = max(q1, q0 + 1);
         }
         __syncthreads();
-        const uint32_t p1 = s_p1, nb = p1 - p0;
-        const uint32_t cnt = build_sorted(a, m, rs, p0, p1, use_mask && !internal, !internal, s_hist, &s_count);
+        const uint32_t q1 = s_p1, nb = q1 - q0;
+        // the internal pass takes nodes [0, n_int); a leaf batch positions
+        // [q0, q1) of the leaf sequence
+        const uint32_t cnt = build_sorted(a, m, rs, internal ? 0u : q0, q1, internal ? nullptr : seq,
+                                          internal ? 0u : a.n_int, !internal, s_hist, &s_count);
         decode_sorted<OffT>(a, m, s_digit, cnt, rs, !internal);
         __syncthreads();
         if (internal) {
-            for (uint32_t q0 = 0; q0 < a.n_int;) {
-                const uint32_t lvl = node_level(m.node[q0]);
-                uint32_t q1 = q0;
-                while (q1 < a.n_int && node_level(m.node[q1]) == lvl)
-                    q1++;
+            for (uint32_t b0 = 0; b0 < a.n_int;) {
+                const uint32_t lvl = node_level(m.node[b0]);
+                uint32_t b1 = b0;
+                while (b1 < a.n_int && node_level(m.node[b1]) == lvl)
+                    b1++;
                 const uint4 *src = reinterpret_cast<const uint4 *>(lvl + 2 == a.L ? m.top : m.inter);
                 uint4 *dst = reinterpret_cast<uint4 *>(m.inter);
                 constexpr uint32_t kQ = kSlab / 8;   // uint4 per node slab
-                for (uint32_t i = tid; i < (q1 - q0) * kQ; i += kThreads) {
-                    const uint32_t p = q0 + i / kQ, rest = i % kQ;
+                for (uint32_t i = tid; i < (b1 - b0) * kQ; i += kThreads) {
+                    const uint32_t p = b0 + i / kQ, rest = i % kQ;
                     const uint4 s4 = src[node_parent(m.node[p]) * kQ + rest];
                     uint4 d4 = dst[p * kQ + rest];
                     d4.x = d4.x + s4.x - kB2;
@@ -531,30 +561,18 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
                     dst[p * kQ + rest] = d4;
                 }
                 __syncthreads();
-                q0 = q1;
+                b0 = b1;
             }
-            // the unsorted list may have covered the zero slot
-            for (uint32_t i = tid; i < kVals / 2; i += kThreads)
-                reinterpret_cast<uint32_t *>(m.res + kZeroSlot * kVals)[i] = kB2;
-            for (uint32_t p = a.n_int + tid; p < a.S; p += kThreads) {
-                uint32_t c = 0;
-                if (!use_mask || a.needed[node_view(m.node[p])])
-                    for (uint32_t r = 0; r < kRecs; r++)
-                        c += (m.mask[r * a.MW + (p >> 5)] >> (p & 31u)) & 1u;
-                m.leafcnt[p - a.n_int] = (uint16_t)c;
-            }
+            prepare_leaves();
             internal = false;
-            p0 = a.n_int;
             continue;
         }
         // parent + residual -> RGB: one view per warp step, lane = (block
         // row, location), four pixels per lane written straight to the
         // output row
         for (uint32_t j = warp; j < nb; j += kWarps) {
-            const uint32_t info = m.node[p0 + j];
+            const uint32_t info = m.node[leaf_node(q0 + j)];
             const uint32_t view = node_view(info);
-            if (use_mask && !a.needed[view])
-                continue;
             const uint32_t row = (uint32_t)lane / kStrip, loc = (uint32_t)lane % kStrip;
             const uint32_t y = by * 4 + row, x = (bx0 + loc) * 4;
             if (loc >= nl || y >= a.H)
@@ -604,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
                 }
             }
         }
-        p0 = p1;
+        q0 = q1;
     }
 }
 

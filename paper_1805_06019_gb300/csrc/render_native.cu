@@ -43,15 +43,12 @@ constexpr int kListCap = 1024;          // views collected per pass
 constexpr int kGroupCap = 64;           // views whose parameters are cached per group
 constexpr int kMaxNeed = 4 * kMaxLevels;
 constexpr uint32_t kSmemBytes = 64 * 1024;
-// Batches of at least this many cameras decode their neighbour views first
-// (one pass over every record, then a cheap blend per camera); a single
-// camera decodes block by block inside the render kernel.  Views of 2^20
-// pixels or more switch one camera later: there the first path's pass over
-// every record (about 0.4 ms for 17 x 17 views of 1024^2) outweighs two
-// cameras' on-demand decode.
+// Batches of at least this many cameras decode the neighbour views they need
+// first (one pass over every record, the needed views only, then a cheap
+// blend per camera); a single camera decodes block by block inside the
+// render kernel, which is faster for it (0.27 against 0.37 ms for a 1024^2
+// view of a 17 x 17 light field).
 constexpr uint32_t kDecodeFirstViews = 2;
-constexpr uint32_t kDecodeFirstViewsLarge = 3;
-constexpr size_t kLargeViewPixels = size_t(1) << 20;
 
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
 
@@ -781,8 +778,7 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     void *scratch = nullptr;
     const size_t view_words = (size_t)a.W * a.H;
     const size_t mask_bytes = (a.sv.n_views + 255) / 256 * 256;
-    const uint32_t first_from = view_words >= kLargeViewPixels ? kDecodeFirstViewsLarge : kDecodeFirstViews;
-    if (n >= first_from &&
+    if (n >= kDecodeFirstViews &&
         cudaMallocAsync(&scratch, mask_bytes + 4 * view_words * a.sv.n_views, st) == cudaSuccess) {
         uint8_t *needed = static_cast<uint8_t *>(scratch);
         uint32_t *decoded = reinterpret_cast<uint32_t *>(needed + mask_bytes);
