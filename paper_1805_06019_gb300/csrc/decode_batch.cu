@@ -283,10 +283,18 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
                 }
                 __syncwarp();
                 // ReadBlock(RKV^n, BlkIdx): the accumulators start at the top RKV
-                for (uint32_t i = lane; i < ns * 48; i += 32) {
-                    const uint32_t slot = i / 48, k = i - slot * 48;
+                // (96 bytes per slot, as six 16-byte loads)
+                for (uint32_t i = lane; i < ns * 6; i += 32) {
+                    const uint32_t slot = i / 6, k = i - slot * 6;
                     const uint32_t top = view_anc[s_view[slot] * kMaxLevels + a.L - 1];
-                    s_acc[i] = a.top[((size_t)top * a.nloc + loc) * 48 + k];
+                    const uint4 v = reinterpret_cast<const uint4 *>(a.top + ((size_t)top * a.nloc + loc) * 48)[k];
+                    int32_t *d = s_acc + slot * 48 + k * 8;
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        d[2 * e] = (int32_t)(int16_t)(w[e] & 0xFFFFu);
+                        d[2 * e + 1] = (int32_t)w[e] >> 16;
+                    }
                 }
                 // stored ancestor blocks of these requests, compacted
                 const uint32_t ntask = ns * 3 * nl;
