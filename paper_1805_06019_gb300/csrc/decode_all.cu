@@ -2,27 +2,31 @@
 //
 // One CTA owns a strip of kStrip consecutive block locations of one block
 // row; their 3 * kStrip records (location-major, then Y / Co / Cg) and
-// top-RKV blocks are read once.  Phases:
+// top-RKV blocks are read once (the records staged in shared memory when they
+// fit).  Phases:
 //  1. scan: one warp per record counts the stored blocks (popcounts of the
 //     presence mask) and turns the closed-form payload lengths of their
 //     headers into payload offsets with a warp scan;
-//  2. internal nodes (levels >= 1, first in BFS order): the stored blocks are
-//     compacted into a work list (no thread idles on an absent node) and each
-//     thread decodes whole blocks with a sequential bit reader; the levels are
-//     then added top-down: reconstruction = parent reconstruction (or top
-//     RKV) + residual;
+//  2. internal nodes (levels >= 1, first in BFS order): their stored blocks
+//     are compacted into a work list with their headers and sorted by BISE
+//     mode, so that a warp decodes 32 blocks of one mode with that mode's
+//     straight-line decoder (one thread per block); the levels are then added
+//     top-down: reconstruction = parent reconstruction (or top RKV) +
+//     residual;
 //  3. the views (leaves), as many at a time (up to kLeafMax) as have at most
-//     kResCap stored blocks over the strip: compacted, decoded the same way
-//     into compact slots (a per-(view, record) map points at them; absent
-//     blocks add nothing), then parent + residual is converted from YCoCg-R
-//     to RGB and written as whole image rows with 16-byte stores.
-// Every stored block of the strip is decoded once and every output byte is
-// written once.
+//     kResCap stored blocks over the strip: listed, sorted and decoded the
+//     same way into compact slots (a per-(view, record) map points at them;
+//     absent blocks read a slot of zeros), then parent + residual goes
+//     through the inverse YCoCg-R two pixels at a time and each lane writes
+//     its four pixels straight to the output row.
+// Reconstructions are 16-bit values plus a bias of 2^14, two to a word (the
+// loader refuses streams whose values could leave that range).  Every stored
+// block of the strip is decoded once and every output byte is written once.
 //
 // A second instantiation writes one packed RGB word per pixel (r | g << 8 |
-// b << 16) and decodes only the views a per-view mask asks for; the renderer
-// uses it to decode, from the compressed stream, just the views a batch of
-// new cameras samples.
+// b << 16) and decodes only the views a per-view mask asks for (its leaf
+// batches run over the needed views alone); the renderer uses it to decode,
+// from the compressed stream, just the views a batch of new cameras samples.
 #include <cuda_runtime.h>
 
 #include <algorithm>
