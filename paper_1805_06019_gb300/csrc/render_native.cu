@@ -26,7 +26,6 @@
 //  4. per view, each thread blends one column of 4 pixels, sliding a 2 x 2
 //     stencil down the window (lanes read consecutive words, no bank
 //     conflicts), and writes with streaming stores.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -149,13 +148,21 @@ __host__ __device__ __forceinline__ uint32_t window_words(int tw, int th, int sx
     return 2u * (uint32_t)(tw + 2 + sx) * (uint32_t)(th + 1 + sy);
 }
 
-// A window pixel: R, G and B as halves (8-bit values are exact in fp16).
-__device__ __forceinline__ uint2 rgb_half(uint32_t rgb24)
+// A window pixel, two words that unpack to floats with one shift or mask
+// each (win_r, win_g, win_b): R and G as bf16 halves, B as a float; 8-bit
+// values are exact in both.
+__device__ __forceinline__ uint2 rgb_window(uint32_t rgb24)
 {
-    const __half2 rg = __floats2half2_rn((float)(rgb24 & 255u), (float)((rgb24 >> 8) & 255u));
-    const __half2 b0 = __floats2half2_rn((float)((rgb24 >> 16) & 255u), 0.0f);
-    return make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
+    // bf16: R in the low half, G in the high half of one word; B as a full
+    // float (8-bit integers have no bits below the top 16)
+    const uint32_t r = __float_as_uint((float)(rgb24 & 255u)) >> 16;
+    const uint32_t g = __float_as_uint((float)((rgb24 >> 8) & 255u));
+    const uint32_t b = __float_as_uint((float)((rgb24 >> 16) & 255u));
+    return make_uint2(g | r, b);
 }
+__device__ __forceinline__ float win_r(uint2 p) { return __uint_as_float(p.x << 16); }
+__device__ __forceinline__ float win_g(uint2 p) { return __uint_as_float(p.x & 0xFFFF0000u); }
+__device__ __forceinline__ float win_b(uint2 p) { return __uint_as_float(p.y); }
 
 // One out-of-line copy of the block decoder keeps the kernel's code small
 // enough for the instruction cache.
@@ -448,23 +455,23 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     }
                     uint2 *da = reinterpret_cast<uint2 *>(g_dyn + wa.f_off) + ra * wa.FW;
                     if (lane < wa.WX)
-                        da[lane] = rgb_half(va0);
+                        da[lane] = rgb_window(va0);
                     if (lane + 32 < wa.WX)
-                        da[lane + 32] = rgb_half(va1);
+                        da[lane + 32] = rgb_window(va1);
                     if (lane + 64 < wa.WX)
-                        da[lane + 64] = rgb_half(va2);
+                        da[lane + 64] = rgb_window(va2);
                     for (int cc = 96 + lane; cc < wa.WX; cc += 32)   // spreads wider than 96 pixels
-                        da[cc] = rgb_half(__ldg(sa + min(max(wa.wx0 + cc, 0), (int)a.W - 1)));
+                        da[cc] = rgb_window(__ldg(sa + min(max(wa.wx0 + cc, 0), (int)a.W - 1)));
                     if (has_b) {
                         uint2 *db = reinterpret_cast<uint2 *>(g_dyn + wb.f_off) + r_b * wb.FW;
                         if (lane < wb.WX)
-                            db[lane] = rgb_half(vb0);
+                            db[lane] = rgb_window(vb0);
                         if (lane + 32 < wb.WX)
-                            db[lane + 32] = rgb_half(vb1);
+                            db[lane + 32] = rgb_window(vb1);
                         if (lane + 64 < wb.WX)
-                            db[lane + 64] = rgb_half(vb2);
+                            db[lane + 64] = rgb_window(vb2);
                         for (int cc = 96 + lane; cc < wb.WX; cc += 32)
-                            db[cc] = rgb_half(__ldg(sb + min(max(wb.wx0 + cc, 0), (int)a.W - 1)));
+                            db[cc] = rgb_window(__ldg(sb + min(max(wb.wx0 + cc, 0), (int)a.W - 1)));
                     }
                 }
                 __syncthreads();
@@ -554,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     if (px < wn.cx0 || px > wn.cx1 || py < wn.cy0 || py > wn.cy1)
                         continue;
                     const int sh16 = 16 * (v & 1);
-                    const uint2 rgb = rgb_half(ycocg_to_rgb24((int16_t)(pk[0][v >> 1] >> sh16),
+                    const uint2 rgb = rgb_window(ycocg_to_rgb24((int16_t)(pk[0][v >> 1] >> sh16),
                                                               (int16_t)(pk[1][v >> 1] >> sh16),
                                                               (int16_t)(pk[2][v >> 1] >> sh16)));
                     // window columns whose clamped x is px (more than one on the image edge)
@@ -598,23 +605,19 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                     float a0[3], a1[3];
                     {
                         const uint2 p0 = f[0], p1 = f[1];
-                        const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&p0.x));
-                        const float2 rg1 = __half22float2(*reinterpret_cast<const __half2 *>(&p1.x));
-                        a0[0] = rg0.x;
-                        a0[1] = rg0.y;
-                        a0[2] = __low2float(*reinterpret_cast<const __half2 *>(&p0.y));
-                        a1[0] = rg1.x;
-                        a1[1] = rg1.y;
-                        a1[2] = __low2float(*reinterpret_cast<const __half2 *>(&p1.y));
+                        a0[0] = win_r(p0);
+                        a0[1] = win_g(p0);
+                        a0[2] = win_b(p0);
+                        a1[0] = win_r(p1);
+                        a1[1] = win_g(p1);
+                        a1[2] = win_b(p1);
                     }
 #pragma unroll
                     for (int rr = 0; rr < kRows; rr++) {
                         f += fw;
                         const uint2 p0 = f[0], p1 = f[1];
-                        const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&p0.x));
-                        const float2 rg1 = __half22float2(*reinterpret_cast<const __half2 *>(&p1.x));
-                        const float b0[3] = {rg0.x, rg0.y, __low2float(*reinterpret_cast<const __half2 *>(&p0.y))};
-                        const float b1[3] = {rg1.x, rg1.y, __low2float(*reinterpret_cast<const __half2 *>(&p1.y))};
+                        const float b0[3] = {win_r(p0), win_g(p0), win_b(p0)};
+                        const float b1[3] = {win_r(p1), win_g(p1), win_b(p1)};
 #pragma unroll
                         for (int ch = 0; ch < 3; ch++) {
                             // one FMA per tap, in the order 00, 10, 01, 11
