@@ -590,42 +590,53 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                 if (!active)
                     continue;
                 const ViewP &vp = s_vp[q - g0];
-                float acc[kRows][3];
+                // R and G accumulate as a pair (one paired FMA per tap), B on
+                // its own; the taps are added in the order 00, 10, 01, 11
+                float2 acc_rg[kRows];
+                float acc_b[kRows];
 #pragma unroll
-                for (int rr = 0; rr < kRows; rr++)
-                    acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
+                for (int rr = 0; rr < kRows; rr++) {
+                    acc_rg[rr] = make_float2(0.0f, 0.0f);
+                    acc_b[rr] = 0.0f;
+                }
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     if (!((vp.used >> k) & 1u))
                         continue;
                     const float4 wk = *reinterpret_cast<const float4 *>(vp.w[k]);
-                    const float w00 = wk.x, w10 = wk.y, w01 = wk.z, w11 = wk.w;
+                    const float2 w00 = make_float2(wk.x, wk.x), w10 = make_float2(wk.y, wk.y);
+                    const float2 w01 = make_float2(wk.z, wk.z), w11 = make_float2(wk.w, wk.w);
                     const int fw = win_fw[k];
                     const uint2 *f = win_at[k] + vp.base[k];
-                    float a0[3], a1[3];
+                    float2 a0, a1;
+                    float a0b, a1b;
                     {
                         const uint2 p0 = f[0], p1 = f[1];
-                        a0[0] = win_r(p0);
-                        a0[1] = win_g(p0);
-                        a0[2] = win_b(p0);
-                        a1[0] = win_r(p1);
-                        a1[1] = win_g(p1);
-                        a1[2] = win_b(p1);
+                        a0 = make_float2(win_r(p0), win_g(p0));
+                        a1 = make_float2(win_r(p1), win_g(p1));
+                        a0b = win_b(p0);
+                        a1b = win_b(p1);
                     }
 #pragma unroll
                     for (int rr = 0; rr < kRows; rr++) {
                         f += fw;
                         const uint2 p0 = f[0], p1 = f[1];
-                        const float b0[3] = {win_r(p0), win_g(p0), win_b(p0)};
-                        const float b1[3] = {win_r(p1), win_g(p1), win_b(p1)};
-#pragma unroll
-                        for (int ch = 0; ch < 3; ch++) {
-                            // one FMA per tap, in the order 00, 10, 01, 11
-                            acc[rr][ch] = fmaf(w11, b1[ch], fmaf(w01, b0[ch], fmaf(w10, a1[ch], fmaf(w00, a0[ch], acc[rr][ch]))));
-                            a0[ch] = b0[ch];
-                            a1[ch] = b1[ch];
-                        }
+                        const float2 b0 = make_float2(win_r(p0), win_g(p0)), b1 = make_float2(win_r(p1), win_g(p1));
+                        const float b0b = win_b(p0), b1b = win_b(p1);
+                        acc_rg[rr] = __ffma2_rn(w11, b1, __ffma2_rn(w01, b0, __ffma2_rn(w10, a1, __ffma2_rn(w00, a0, acc_rg[rr]))));
+                        acc_b[rr] = fmaf(w11.x, b1b, fmaf(w01.x, b0b, fmaf(w10.x, a1b, fmaf(w00.x, a0b, acc_b[rr]))));
+                        a0 = b0;
+                        a1 = b1;
+                        a0b = b0b;
+                        a1b = b1b;
                     }
+                }
+                float acc[kRows][3];
+#pragma unroll
+                for (int rr = 0; rr < kRows; rr++) {
+                    acc[rr][0] = acc_rg[rr].x;
+                    acc[rr][1] = acc_rg[rr].y;
+                    acc[rr][2] = acc_b[rr];
                 }
                 const uint32_t r = s_list[q];
 #pragma unroll
