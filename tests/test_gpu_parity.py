@@ -282,6 +282,29 @@ def test_plain_render_1000_views_sampled(rlfc, plain):
     _check_render(out[0].cpu().numpy(), want0, RENDER_U8_MIN_EQUAL)
 
 
+def test_plain_single_cameras_equal_batched_ones(rlfc, plain):
+    # one camera on the 9 x 9 grid of 512^2 views takes the on-demand path
+    # with persistent CTAs over the occupied cell's tiles (256 tiles x 64
+    # cells is far more CTAs than the GPU holds); a batch of cameras decodes
+    # the views first.  Both must give the same bits, and the oracle's view
+    p, _, streams = plain
+    data = streams[4]
+    lf = oracle.Stream(data).decode_all(nthreads=8)
+    cams = lf_synth.random_views(6, p["U"], p["V"], 77, d_choices=p["disparities"])
+    cams[0, :2] = (0.0, 0.0)                                  # a grid corner
+    cams[1, :2] = (p["U"] - 1.0, p["V"] - 1.0)                # the opposite corner
+    st = rlfc.Stream(data)
+    W, H = p["render_size"]
+    uv = torch.from_numpy(cams[:, :2].copy()).cuda()
+    disp = torch.from_numpy(cams[:, 2].copy()).cuda()
+    batch = st.render(uv, disp, W, H).cpu().numpy()
+    for r in range(len(cams)):
+        one = st.render(uv[r:r + 1], disp[r:r + 1], W, H).cpu().numpy()[0]
+        assert np.array_equal(one, batch[r]), r
+    want = oracle.render_view(lf, p["U"], p["V"], float(cams[2, 0]), float(cams[2, 1]), float(cams[2, 2]), W, H)
+    _check_render(batch[2], want)
+
+
 def _u8_of_float32(x: np.ndarray) -> np.ndarray:
     """floor(clamp(v, 0, 1) * 255 + 0.5) with each operation rounded in float32."""
     v = np.clip(x.astype(np.float32), np.float32(0), np.float32(1))
