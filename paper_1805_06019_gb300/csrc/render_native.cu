@@ -160,7 +160,7 @@ __device__ __forceinline__ uint2 rgb_window(uint32_t rgb24)
     const uint32_t b = __float_as_uint((float)((rgb24 >> 16) & 255u));
     return make_uint2(g | r, b);
 }
-__device__ __forceinline__ float win_r(uint2 p) { return __uint_as_float(p.x << 16); }
+__device__ __forceinline__ float win_r(uint2 p) { return __uint_as_float(__byte_perm(p.x, 0u, 0x1044)); }   // p.x << 16
 __device__ __forceinline__ float win_g(uint2 p) { return __uint_as_float(p.x & 0xFFFF0000u); }
 __device__ __forceinline__ float win_b(uint2 p) { return __uint_as_float(p.y); }
 
