@@ -70,6 +70,7 @@ struct Args {
     const uint32_t *node_info;
     uint8_t *out;          // RGB bytes, or packed RGB words (packed instantiation)
     const uint8_t *needed; // packed instantiation: per-view mask (nonzero = decode), may be null
+    const uint32_t *slot_of; // packed instantiation with a mask: output slot of each needed view
     uint32_t S, n_int, n_top, L, q, MW;
     uint32_t nlx, nloc, W, H;
     uint32_t out_aligned16; // output base is 16-byte aligned
@@ -601,7 +602,8 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
                                         __byte_perm(t01, b01, 0x0632) & 0xFFFFFFu,
                                         __byte_perm(t23, b23, 0x0410) & 0xFFFFFFu,
                                         __byte_perm(t23, b23, 0x0632) & 0xFFFFFFu};
-                uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)view * a.H + y) * a.W + x;
+                const uint32_t ov = a.slot_of ? a.slot_of[view] : view;
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.out) + ((size_t)ov * a.H + y) * a.W + x;
                 if (whole && a.out_aligned16 && (a.W & 3u) == 0) {
                     *reinterpret_cast<uint4 *>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
                 } else {
@@ -631,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 4) decode_all_kernel(const Args a)
 }
 
 template <bool kPacked>
-int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, cudaStream_t st)
+int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, const uint32_t *slot_of, cudaStream_t st)
 {
     const Tables &t = s->tab;
     Args a;
@@ -641,6 +643,7 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.node_info = s->d_node_info;
     a.out = d_out;
     a.needed = needed;
+    a.slot_of = slot_of;
     a.S = t.S;
     a.n_int = t.n_int;
     a.n_top = t.n_top;
@@ -686,12 +689,13 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
 
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st)
 {
-    return launch_decode<false>(s, d_out, nullptr, st);
+    return launch_decode<false>(s, d_out, nullptr, nullptr, st);
 }
 
-int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, cudaStream_t st)
+int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, const uint32_t *slot_of,
+                         cudaStream_t st)
 {
-    return launch_decode<true>(s, reinterpret_cast<uint8_t *>(d_out), needed, st);
+    return launch_decode<true>(s, reinterpret_cast<uint8_t *>(d_out), needed, slot_of, st);
 }
 
 }  // namespace rlfc

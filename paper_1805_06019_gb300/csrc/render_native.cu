@@ -44,10 +44,13 @@ constexpr int kMaxNeed = 4 * kMaxLevels;
 constexpr uint32_t kSmemBytes = 64 * 1024;
 // Batches of at least this many cameras decode the neighbour views they need
 // first (one pass over every record, the needed views only, then a cheap
-// blend per camera); a single camera decodes block by block inside the
-// render kernel, which is faster for it (0.27 against 0.37 ms for a 1024^2
-// view of a 17 x 17 light field).
-constexpr uint32_t kDecodeFirstViews = 2;
+// blend per camera); smaller ones decode block by block inside the render
+// kernel.  Measured on 17 x 17 views of 1024^2: 4 cameras take 0.51 ms the
+// first way and 1.0 ms the second; 1 camera 0.37 against 0.27 ms.  Under a
+// serving load of many small calls on several streams, decoding first for
+// two or three cameras (a full-GPU pass over every record each time)
+// saturated the GPU at 5000 requests/s, so the switch sits at four.
+constexpr uint32_t kDecodeFirstViews = 4;
 
 __constant__ uint32_t c_modes[kNumModes] = RLFC_MODE_TABLE_INIT;
 
@@ -57,7 +60,8 @@ struct Args {
     const float *disp;
     float *out;
     uint8_t *out8;             // when set, 8-bit RGB goes here instead of out
-    const uint32_t *decoded;   // packed RGB views [view][H][W] decoded for this call, or null
+    const uint32_t *decoded;   // packed RGB views [slot][H][W] decoded for this call, or null
+    const uint32_t *slot_of;   // with decoded views: the slot of each view
     uint32_t U, V, W, H, n;
     uint32_t tiles_x, cells_u;
     uint32_t n_tiles;           // tiles per view
@@ -442,8 +446,8 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         locate(rb, kb, r_b);
                     const Window &wa = s_win[ka];
                     const Window &wb = s_win[kb];
-                    const uint32_t *sa = a.decoded + ((size_t)nview[ka] * a.H + min(max(wa.wy0 + ra, 0), (int)a.H - 1)) * a.W;
-                    const uint32_t *sb = a.decoded + ((size_t)nview[kb] * a.H + min(max(wb.wy0 + r_b, 0), (int)a.H - 1)) * a.W;
+                    const uint32_t *sa = a.decoded + ((size_t)a.slot_of[nview[ka]] * a.H + min(max(wa.wy0 + ra, 0), (int)a.H - 1)) * a.W;
+                    const uint32_t *sb = a.decoded + ((size_t)a.slot_of[nview[kb]] * a.H + min(max(wb.wy0 + r_b, 0), (int)a.H - 1)) * a.W;
                     uint32_t va0, va1, va2, vb0 = 0u, vb1 = 0u, vb2 = 0u;
                     va0 = lane < wa.WX ? __ldg(sa + min(max(wa.wx0 + lane, 0), (int)a.W - 1)) : 0u;
                     va1 = lane + 32 < wa.WX ? __ldg(sa + min(max(wa.wx0 + lane + 32, 0), (int)a.W - 1)) : 0u;
@@ -702,6 +706,43 @@ __global__ void __launch_bounds__(kListThreads) list_cells_kernel(const Args a, 
         *count = total;
 }
 
+// Numbers the marked views 0, 1, ... in view order (one CTA; at most 16383
+// views, 16 per thread): slot_of[v] for a marked view v.
+__global__ void __launch_bounds__(kListThreads) assign_slots_kernel(const uint8_t *needed, uint32_t n_views,
+                                                                    uint32_t *slot_of)
+{
+    __shared__ uint32_t s_warp[kListThreads / 32];
+    const uint32_t per = (n_views + kListThreads - 1) / kListThreads;
+    const uint32_t v0 = threadIdx.x * per, v1 = min(n_views, v0 + per);
+    uint32_t cnt = 0;
+    for (uint32_t v = v0; v < v1; v++)
+        cnt += needed[v] != 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d)
+            incl += y;
+    }
+    if (lane == 31)
+        s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+            if (lane >= d)
+                w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t at = incl - cnt + (warp ? s_warp[warp - 1] : 0u);
+    for (uint32_t v = v0; v < v1; v++)
+        if (needed[v])
+            slot_of[v] = at++;
+}
+
 // Marks the neighbour views that each camera blends with a non-zero weight.
 __global__ void mark_needed_kernel(const Args a, uint8_t *needed)
 {
@@ -786,25 +827,33 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
         { rlfc::TraceScope trace_("list_cells_kernel", st); list_cells_kernel<<<1, kListThreads, 0, st>>>(a, n_cells, cells, cells + n_cells); }
     }
     // Batches of many views decode the views they need once into a transient
-    // packed-RGB buffer (stream-ordered allocation, freed on the same stream);
-    // small batches decode block by block inside the render kernel.
+    // packed-RGB buffer (stream-ordered allocation, freed on the same stream),
+    // one slot per needed view: a camera needs at most four views, so
+    // min(views, 4n) slots suffice.  Small batches decode block by block
+    // inside the render kernel.
     a.decoded = nullptr;
+    a.slot_of = nullptr;
     void *scratch = nullptr;
     const size_t view_words = (size_t)a.W * a.H;
     const size_t mask_bytes = (a.sv.n_views + 255) / 256 * 256;
+    const size_t slot_bytes = (4ull * a.sv.n_views + 255) / 256 * 256;
+    const size_t n_slots = std::min<size_t>(a.sv.n_views, 4ull * n);
     if (n >= kDecodeFirstViews &&
-        cudaMallocAsync(&scratch, mask_bytes + 4 * view_words * a.sv.n_views, st) == cudaSuccess) {
+        cudaMallocAsync(&scratch, mask_bytes + slot_bytes + 4 * view_words * n_slots, st) == cudaSuccess) {
         uint8_t *needed = static_cast<uint8_t *>(scratch);
-        uint32_t *decoded = reinterpret_cast<uint32_t *>(needed + mask_bytes);
+        uint32_t *slot_of = reinterpret_cast<uint32_t *>(needed + mask_bytes);
+        uint32_t *decoded = reinterpret_cast<uint32_t *>(needed + mask_bytes + slot_bytes);
         int rc = RLFC_OK;
         if ((e = cudaMemsetAsync(needed, 0, mask_bytes, st)) != cudaSuccess)
             rc = cuda_fail(e, "render: clearing the view mask");
         if (rc == RLFC_OK) {
             { rlfc::TraceScope trace_("mark_needed_kernel", st); mark_needed_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, needed); }
-            rc = launch_decode_packed(s, decoded, needed, st);
+            { rlfc::TraceScope trace_("assign_slots_kernel", st); assign_slots_kernel<<<1, kListThreads, 0, st>>>(needed, a.sv.n_views, slot_of); }
+            rc = launch_decode_packed(s, decoded, needed, slot_of, st);
         }
         if (rc == RLFC_OK) {
             a.decoded = decoded;
+            a.slot_of = slot_of;
             { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
             e = cudaGetLastError();
             if (e != cudaSuccess)

@@ -90,7 +90,10 @@ int cuda_fail(cudaError_t e, const char *what);
 
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
 // every view the mask marks (all when null), as packed RGB words [view][H][W]
-int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, cudaStream_t st);
+// Packed RGB words of the views `needed` marks, view v into slot slot_of[v]
+// of d_out ([slot][H][W]); with needed null, every view v into slot v.
+int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, const uint32_t *slot_of,
+                         cudaStream_t st);
 // Largest |value| of any stored block of the stream, decoded (synchronous).
 int block_magnitude(const rlfc_stream *s, cudaStream_t st, uint32_t *mag);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,
