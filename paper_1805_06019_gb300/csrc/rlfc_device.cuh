@@ -151,7 +151,9 @@ __device__ __forceinline__ uint32_t ycocg_to_rgb24(int y, int co, int cg)
 // equals that of the same float operations anywhere else.
 __device__ __forceinline__ uint8_t to_u8(float v)
 {
-    return (uint8_t)floorf(__fadd_rn(__fmul_rn(fminf(fmaxf(v, 0.0f), 1.0f), 255.0f), 0.5f));
+    // __saturatef clamps to [0, 1] (NaN to 0); the argument of the
+    // round-down conversion is at least 0.5, so it is the floor
+    return (uint8_t)__float2uint_rd(__fadd_rn(__fmul_rn(__saturatef(v), 255.0f), 0.5f));
 }
 
 // Store a rendered RGB pixel (pixel index px) as floats, or as 8 bits when
