@@ -45,8 +45,8 @@ UNIT = "Mpix/s"
 # kernel); a kernel missing here reports null
 TRAFFIC_PER_LAUNCH = {
     # render_native_kernel, first timed step of `bench.py --steps 2 --warmup 1` (ncu one-pass
-    # dram__bytes_read.sum 86.25 MB + dram__bytes_write.sum 3.08 GB)
-    ("plain", 4, 1000, "render_native_kernel"): 86_250_000 + 3_080_000_000,
+    # dram__bytes_read.sum 85.90 MB + dram__bytes_write.sum 3.08 GB)
+    ("plain", 4, 1000, "render_native_kernel"): 85_900_000 + 3_080_000_000,
 }
 
 
