@@ -49,6 +49,19 @@ TRAFFIC_PER_LAUNCH = {
     ("plain", 4, 1000, "render_native_kernel"): 85_900_000 + 3_080_000_000,
 }
 
+# smsp__inst_executed.sum of one launch (warp instructions), from the same kind
+# of one-pass ncu capture (`--metrics smsp__inst_executed.sum ... -s 3 -c 3`
+# on `bench.py --steps 2 --warmup 1`); the kernels are integer and
+# conversion work bound by instruction issue more than by DRAM
+INSTR_PER_LAUNCH = {
+    ("plain", 4, 1000, "render_native_kernel"): 1_081_018_112,
+    ("plain", 4, 1000, "decode_all_kernel"): 70_592_100,
+    ("plain", 4, 1000, "decode_all_kernel<packed>"): 76_710_223,
+}
+# issue peak: 152 SMs x 4 schedulers x one warp instruction per cycle at the
+# 2070 MHz maximum SM clock
+ISSUE_PEAK = 152 * 4 * 2.070e9
+
 
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -312,11 +325,21 @@ def run_ours(args):
         gbs = kbytes.get(name, 0) / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
         kernels[name] = {"launches": launches, "avg_ms": avg, "share": tot / max(sum(t for _, t in trace.values()), 1e-9),
                          "algorithmic_bytes": kbytes.get(name), "gbs": gbs, "hbm_frac": gbs / peak}
+        instr = INSTR_PER_LAUNCH.get((args.config, tau, n_render, name))
+        if instr is not None and avg > 0:
+            kernels[name]["issue_frac"] = instr / (avg * 1e-3) / ISSUE_PEAK
     top = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
     roof = {"bound": "hbm", "kernel": top, "achieved": kernels[top]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": kernels[top]["gbs"] / peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)",
             "traffic": TRAFFIC_PER_LAUNCH.get((args.config, tau, n_render, top)),
             "bytes_per_launch": kernels[top]["algorithmic_bytes"], "avg_launch_ms": kernels[top]["avg_ms"]}
+    instr_top = INSTR_PER_LAUNCH.get((args.config, tau, n_render, top))
+    if instr_top is not None:
+        # the same kernel against the instruction-issue ceiling
+        ach = instr_top / (kernels[top]["avg_ms"] * 1e-3)
+        roof["issue"] = {"achieved": ach, "peak": ISSUE_PEAK, "unit": "warp instructions/s", "frac": ach / ISSUE_PEAK,
+                         "instructions_per_launch": instr_top,
+                         "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction/cycle x 2070 MHz"}
     gpu_launches = sum(l for l, _ in trace.values())
 
     # end to end through the C ABI: per-step camera upload from pinned host
