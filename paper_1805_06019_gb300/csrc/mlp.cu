@@ -412,31 +412,104 @@ __global__ void __launch_bounds__(kThreads) mlp_loss_grad_kernel(const uint16_t 
         atomicAdd(loss, s_loss);
 }
 
+// Inference, register blocked: each warp takes 4 samples at a time and lane l
+// the outputs l, l + 32, ...; per input feature, one 16-byte broadcast of the
+// 4 samples' activations and one weight per output feed 4 FMAs.  The
+// activations of a warp's samples are its own columns of [feature][sample]
+// arrays (row stride kRowT keeps the 16-byte stores on distinct banks), so the
+// warps never wait on one another after the weights are loaded.
+constexpr int kRowT = kTile + 4;
+
+template <int K, int N, bool kRelu>
+__device__ __forceinline__ void dense_cols(const float *inT, const float *wt, const float *b, int lane, int col,
+                                           float acc[4][(N + 31) / 32])
+{
+    constexpr int kO = (N + 31) / 32;
+#pragma unroll
+    for (int i = 0; i < kO; i++) {
+        const int o = lane + 32 * i;
+        const float bias = o < N ? b[o] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            acc[q][i] = bias;
+    }
+#pragma unroll 4
+    for (int k = 0; k < K; k++) {
+        const float4 v = *reinterpret_cast<const float4 *>(inT + k * kRowT + col);
+#pragma unroll
+        for (int i = 0; i < kO; i++) {
+            const int o = lane + 32 * i;
+            const float w = o < N ? wt[k * N + o] : 0.0f;
+            acc[0][i] = fmaf(v.x, w, acc[0][i]);
+            acc[1][i] = fmaf(v.y, w, acc[1][i]);
+            acc[2][i] = fmaf(v.z, w, acc[2][i]);
+            acc[3][i] = fmaf(v.w, w, acc[3][i]);
+        }
+    }
+    if (kRelu) {
+#pragma unroll
+        for (int i = 0; i < kO; i++)
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                acc[q][i] = fmaxf(acc[q][i], 0.0f);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_cols(float *outT, int lane, int col, const float acc[4][(N + 31) / 32])
+{
+#pragma unroll
+    for (int i = 0; i < (N + 31) / 32; i++) {
+        const int o = lane + 32 * i;
+        if (o < N)
+            *reinterpret_cast<float4 *>(outT + o * kRowT + col) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(const uint16_t *w, const uint16_t *x, uint32_t n,
                                                                 const uint32_t *index, uint8_t *label)
 {
     extern __shared__ __align__(16) float smem[];
     const NetSmem m = carve(smem);
+    float *xT = smem + kP, *h1T = xT + NI * kRowT, *h2T = h1T + NH * kRowT;
     load_weights(w, m);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        load_tile(x, nullptr, nullptr, n, t * kTile, m, nullptr);
-        __syncthreads();
-        forward_tile(m);
-        for (int s = warp; s < kTile; s += kThreads / 32) {
-            const uint32_t gi = t * kTile + s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, col = 4 * warp;
+    const uint32_t ngroups = (n + 3) / 4;
+    for (uint32_t grp = blockIdx.x * (kThreads / 32) + warp; grp < ngroups; grp += gridDim.x * (kThreads / 32)) {
+        const uint32_t s0 = 4 * grp;
+        for (int i = lane; i < 4 * NI; i += 32) {
+            const int q = i / NI, f = i - q * NI;
+            xT[f * kRowT + col + q] = s0 + q < n ? bf(x[(size_t)(s0 + q) * NI + f]) : 0.0f;
+        }
+        __syncwarp();
+        {
+            float a1[4][NH / 32];
+            dense_cols<NI, NH, true>(xT, m.w1t, m.b1, lane, col, a1);
+            store_cols<NH>(h1T, lane, col, a1);
+        }
+        __syncwarp();
+        {
+            float a2[4][NH / 32];
+            dense_cols<NH, NH, true>(h1T, m.w2t, m.b2, lane, col, a2);
+            store_cols<NH>(h2T, lane, col, a2);
+        }
+        __syncwarp();
+        float z[4][(NO + 31) / 32];
+        dense_cols<NH, NO, false>(h2T, m.w3t, m.b3, lane, col, z);
+        // first maximum of each sample's logits over the lanes
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
             float best = -INFINITY;
             int arg = 0;
-            for (int j = lane; j < NO; j += 32) {
-                const float v = m.z[s * NO + j];
-                if (v > best) {
-                    best = v;
-                    arg = j;
+#pragma unroll
+            for (int i = 0; i < (NO + 31) / 32; i++) {
+                const int o = lane + 32 * i;
+                if (o < NO && z[q][i] > best) {
+                    best = z[q][i];
+                    arg = o;
                 }
             }
-            // first maximum over the lanes
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
                 const float ob = __shfl_xor_sync(kFull, best, d);
@@ -446,10 +519,11 @@ __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(const uint16_t *w
                     arg = oa;
                 }
             }
+            const uint32_t gi = s0 + q;
             if (lane == 0 && gi < n)
                 label[index ? index[gi] : gi] = (uint8_t)((arg % kNumModes) | (arg / kNumModes) << 5);
         }
-        __syncthreads();
+        __syncwarp();   // the next group overwrites this warp's columns
     }
 }
 
@@ -612,11 +686,17 @@ RLFC_API int rlfc_mlp_predict(const uint16_t *d_w, const uint16_t *d_x, size_t n
         return RLFC_E_RANGE;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const size_t smem = sizeof(float) * kNetFloats;
+    const size_t smem = sizeof(float) * (kP + (NI + 2 * NH) * kRowT);
     cudaError_t e = cudaFuncSetAttribute(mlp_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "rlfc_mlp_predict");
-    { TraceScope trace_("mlp_predict_kernel", st); mlp_predict_kernel<<<net_grid((uint32_t)n, 4 * sm_count()), kThreads, smem, st>>>(d_w, d_x, (uint32_t)n, d_index, d_label); }
+    // every CTA resident at once (the loop over sample groups is grid-strided)
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_predict_kernel, kThreads, smem)) != cudaSuccess)
+        return cuda_fail(e, "rlfc_mlp_predict");
+    const uint32_t groups = (uint32_t)((n + 4 * (kThreads / 32) - 1) / (4 * (kThreads / 32)));
+    const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(groups, (uint32_t)(std::max(per_sm, 1) * sm_count())));
+    { TraceScope trace_("mlp_predict_kernel", st); mlp_predict_kernel<<<grid, kThreads, smem, st>>>(d_w, d_x, (uint32_t)n, d_index, d_label); }
     e = cudaGetLastError();
     return e == cudaSuccess ? RLFC_OK : cuda_fail(e, "rlfc_mlp_predict");
 }
