@@ -158,6 +158,12 @@ RLFC_API int rlfc_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, co
  * view (i, j) it samples (s + d (i - u), t + d (j - v)) bilinearly with
  * clamp-to-edge, and the four views are blended bilinearly in (u, v).
  * d_out receives n * out_h * out_w * 3 floats (RGB in [0, 1]), view-major.
+ * At native size a call of four or more cameras first decodes the neighbour
+ * views they need into a transient device buffer (stream-ordered
+ * allocation on cuda_stream, released before the call's work completes:
+ * 4 * W * H bytes per needed view, at most min(views, 4n) of them); if that
+ * allocation fails the call decodes on demand instead.  Results do not
+ * depend on the path or on the other views of the call.
  * Errors: RLFC_E_INVALID_ARG, RLFC_E_RANGE, RLFC_E_UNSUPPORTED, RLFC_E_CUDA.
  */
 RLFC_API int rlfc_render_views(const rlfc_stream *s, const float *d_uv, const float *d_disp,
