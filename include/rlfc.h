@@ -456,7 +456,7 @@ RLFC_API int rlfc_trace_read(rlfc_trace_entry *out, size_t cap, size_t *n, int r
  * Learned encoder aid (no counterpart in the paper; it sits beside the encoder
  * and never changes how a stream decodes).  A small network predicts each
  * level-0 block's (shift, mode) from 48 statistics of its residuals; the
- * exhaustive search stays the judge and the fallback (rlfc_encode_ex takes a
+ * exhaustive search stays the arbiter and the fallback (rlfc_encode_ex takes a
  * predicted mode only when it is a candidate).  All pointers are device
  * pointers; every call is asynchronous on `cuda_stream`.
  *
