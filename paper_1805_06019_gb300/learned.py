@@ -1,6 +1,6 @@
 """The learned encoder aid: a network that predicts each level-0 block's
 (shift, mode) from 48 statistics of its residuals, trained on the GPU on the
-exhaustive search's choices, with the search kept as judge and fallback.
+exhaustive search's choices, with the search kept as arbiter and fallback.
 
 Every step runs in librlfc's kernels (rlfc_encode_ex, rlfc_ks_*, rlfc_mlp_*);
 torch holds the device buffers and draws the seeded shuffles.  Decoding is
