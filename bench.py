@@ -388,7 +388,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(h_lf[0].numel() + h_views[0].numel() * h_views[0].element_size()),
                 "steps": e_steps,
                 "note": "downloads of step k overlap step k+1 on a copy stream; the device-to-host link "
-                        "(about 193 GB/s measured on this box) bounds it"}
+                        "(about 193 GB/s measured on GB300 hosts) bounds it"}
 
     e2e = e2e_u8 = None
     if not args.no_e2e:
