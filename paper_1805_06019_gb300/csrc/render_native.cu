@@ -41,7 +41,12 @@ constexpr int kRows = kTH * kTW / kThreads;
 constexpr int kListCap = 1024;          // views collected per pass
 constexpr int kGroupCap = 64;           // views whose parameters are cached per group
 constexpr int kMaxNeed = 4 * kMaxLevels;
-constexpr uint32_t kSmemBytes = 64 * 1024;
+constexpr uint32_t kSmemBytes = 64 * 1024;        // decoding on demand: windows + node table
+// Decoding first: the windows alone, four CTAs per SM (dynamic + static shared
+// memory of four CTAs within the SM's 228 KB)
+constexpr uint32_t kSmemDecoded = 48 * 1024;
+constexpr int kListCapDecoded = 1024;
+constexpr int kGroupCapDecoded = 32;
 // Batches of at least this many cameras decode the neighbour views they need
 // first (one pass over every record, the needed views only, then a cheap
 // blend per camera); smaller ones decode block by block inside the render
@@ -181,11 +186,15 @@ __device__ __noinline__ void decode_block_values(const uint32_t *rec, uint32_t p
 }
 
 
-__global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a)
+template <bool kDecoded>
+__global__ void __launch_bounds__(kThreads, kDecoded ? 4 : 3) render_native_kernel(const Args a)
 {
+    constexpr int kLC = kDecoded ? kListCapDecoded : kListCap;
+    constexpr int kGC = kDecoded ? kGroupCapDecoded : kGroupCap;
+    constexpr uint32_t kSmem = kDecoded ? kSmemDecoded : kSmemBytes;
     __shared__ uint32_t s_mode[kNumModes];
-    __shared__ uint16_t s_list[kListCap];
-    __shared__ ViewP s_vp[kGroupCap];
+    __shared__ uint16_t s_list[kLC];
+    __shared__ ViewP s_vp[kGC];
     __shared__ int s_count, s_gend;
     __shared__ int s_oxmin[4], s_oxmax[4], s_oymin[4], s_oymax[4], s_used[4];
     __shared__ Window s_win[4];
@@ -218,12 +227,12 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
         nview[k] = j * (int)a.U + i;
     }
 
-    for (uint32_t base = 0; base < a.n; base += kListCap) {
-        // ---- phase 1: the views of this cell among [base, base + kListCap)
+    for (uint32_t base = 0; base < a.n; base += kLC) {
+        // ---- phase 1: the views of this cell among [base, base + kLC)
         if (tid == 0)
             s_count = 0;
         __syncthreads();
-        const uint32_t lim = min(a.n, base + kListCap);
+        const uint32_t lim = min(a.n, base + kLC);
         for (uint32_t r = base + tid; r < lim; r += kThreads)
             if (cell_of(a, r) == cell)
                 s_list[atomicAdd(&s_count, 1)] = (uint16_t)r;
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
         const int count = s_count;
         for (int g0 = 0; g0 < count;) {
             // ---- per-view parameters of the next group, in parallel
-            const int gcap = min(kGroupCap, count - g0);
+            const int gcap = min(kGC, count - g0);
             if (tid < 4) {
                 s_oxmin[tid] = s_oymin[tid] = INT_MAX;
                 s_oxmax[tid] = s_oymax[tid] = INT_MIN;
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         vp.used |= 1u << k;
                 }
             }
-            if (tid < kGroupCap) {
+            if (tid < kGC) {
                 // group extents per neighbour: warp reductions, one atomic per warp
                 const bool mine = tid < gcap;
                 const ViewP &vp = s_vp[mine ? tid : 0];
@@ -295,9 +304,9 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         by1 = max(by1, min(max(ty0 + th + oyh[k], 0), (int)a.H - 1) / kBlock);
                     }
                     words = (words + 3) & ~3u;
-                    if (!a.decoded)
+                    if (!kDecoded)
                         words += (uint32_t)((bx1 - bx0 + 1) * (by1 - by0 + 1) * 3 * 2) * a.need_max;
-                    return words * 4 <= kSmemBytes;
+                    return words * 4 <= kSmem;
                 };
                 int ge = g0 + gcap;
                 if (!fits(s_oxmin, s_oxmax, s_oymin, s_oymax, s_used)) {
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                 // BFS positions the used neighbours need, ascending (only
                 // when decoding here)
                 int nn = 0;
-                for (int k = 0; k < 4 && !a.decoded; k++) {
+                for (int k = 0; k < 4 && !kDecoded; k++) {
                     const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
                     s_top[k] = anc[a.sv.L - 1];
                     if (!s_used[k])
@@ -395,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
                         s_need_pos[y] = s_need_pos[y - 1];
                         s_need_pos[y - 1] = tp;
                     }
-                for (int k = 0; k < 4 && !a.decoded; k++) {
+                for (int k = 0; k < 4 && !kDecoded; k++) {
                     const uint32_t *anc = a.sv.view_anc + nview[k] * kMaxLevels;
                     for (uint32_t l = 0; l + 1 < a.sv.L; l++) {
                         int e = -1;
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 3) render_native_kernel(const Args a
             // [1] the block minimum (sign-extended)
             uint32_t *ent = g_dyn + s_ent_off;
 
-            if (a.decoded) {
+            if constexpr (kDecoded) {
                 // ---- phase 2 (decoded views): copy the windows, clamped to the image
                 const int lane = tid & 31, warp = tid >> 5;
                 int rows = 0;
@@ -791,41 +800,17 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     const uint32_t tiles_y = (a.H + kTH - 1) / kTH;
     a.cells_u = a.U > 1 ? a.U - 1 : 1;
     const uint32_t cells_v = a.V > 1 ? a.V - 1 : 1;
-    // a single view (no shift spread) needs four windows of the full tile
-    // and the node table of its footprint
-    a.need_max = 4 * (a.sv.L - 1);
-    const uint32_t single = 4 * (4 * window_words(kTW, kTH, 0, 0) +
-                                 ((kTW + 7) / kBlock + 1) * ((kTH + 7) / kBlock + 1) * 3 * 2 * a.need_max);
-    if (single > kSmemBytes || (uint64_t)a.tiles_x * tiles_y >= (1u << 31) || a.cells_u * cells_v > 65535)
-        return RLFC_E_UNSUPPORTED;
-    cudaError_t e = cudaFuncSetAttribute(render_native_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "render_native: shared memory attribute");
-    a.n_tiles = a.tiles_x * tiles_y;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_native_kernel, kThreads, kSmemBytes)) !=
-            cudaSuccess)
-        return cuda_fail(e, "render_native: occupancy");
     const uint32_t n_cells = a.cells_u * cells_v;
-    dim3 grid(a.n_tiles, n_cells);
-    uint32_t *cells = nullptr;
-    a.cell_list = nullptr;
-    a.cell_count = nullptr;
-    const uint32_t resident = (uint32_t)std::max(sms, 1) * (uint32_t)std::max(per_sm, 1);
-    if (n < 2 * n_cells && (uint64_t)a.n_tiles * n_cells >= 8ull * resident) {
-        // few cameras for a large grid: most of its CTAs would find an empty
-        // cell, so list the occupied cells and run persistent CTAs over their
-        // tiles only (list and count in stream-ordered scratch)
-        grid = dim3(resident);
-        if ((e = cudaMallocAsync(&cells, 4ull * (n_cells + 1), st)) != cudaSuccess)
-            return cuda_fail(e, "render_native: cell list");
-        a.cell_list = cells;
-        a.cell_count = cells + n_cells;
-        { rlfc::TraceScope trace_("list_cells_kernel", st); list_cells_kernel<<<1, kListThreads, 0, st>>>(a, n_cells, cells, cells + n_cells); }
-    }
+    if ((uint64_t)a.tiles_x * tiles_y >= (1u << 31) || n_cells > 65535)
+        return RLFC_E_UNSUPPORTED;
+    a.n_tiles = a.tiles_x * tiles_y;
+    // a single view (no shift spread) needs four windows of the full tile,
+    // and, decoding on demand, the node table of its footprint
+    a.need_max = 4 * (a.sv.L - 1);
+    const uint32_t win1 = 4 * 4 * window_words(kTW, kTH, 0, 0);
+    const uint32_t single = win1 + 4 * ((kTW + 7) / kBlock + 1) * ((kTH + 7) / kBlock + 1) * 3 * 2 * a.need_max;
+    cudaError_t e;
+
     // Batches of many views decode the views they need once into a transient
     // packed-RGB buffer (stream-ordered allocation, freed on the same stream),
     // one slot per needed view: a camera needs at most four views, so
@@ -838,12 +823,47 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     const size_t mask_bytes = (a.sv.n_views + 255) / 256 * 256;
     const size_t slot_bytes = (4ull * a.sv.n_views + 255) / 256 * 256;
     const size_t n_slots = std::min<size_t>(a.sv.n_views, 4ull * n);
-    if (n >= kDecodeFirstViews &&
-        cudaMallocAsync(&scratch, mask_bytes + slot_bytes + 4 * view_words * n_slots, st) == cudaSuccess) {
+    bool first = n >= kDecodeFirstViews && win1 <= kSmemDecoded;
+    if (first && cudaMallocAsync(&scratch, mask_bytes + slot_bytes + 4 * view_words * n_slots, st) != cudaSuccess) {
+        cudaGetLastError();   // a failed stream-ordered allocation only selects the other path
+        first = false;
+    }
+    if (!first && single > kSmemBytes)
+        return RLFC_E_UNSUPPORTED;
+    auto kern = first ? render_native_kernel<true> : render_native_kernel<false>;
+    const uint32_t smem = first ? kSmemDecoded : kSmemBytes;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) {
+        if (scratch)
+            cudaFreeAsync(scratch, st);
+        return cuda_fail(e, "render_native: launch configuration");
+    }
+    dim3 grid(a.n_tiles, n_cells);
+    uint32_t *cells = nullptr;
+    a.cell_list = nullptr;
+    a.cell_count = nullptr;
+    int rc = RLFC_OK;
+    const uint32_t resident = (uint32_t)std::max(sms, 1) * (uint32_t)std::max(per_sm, 1);
+    if (n < 2 * n_cells && (uint64_t)a.n_tiles * n_cells >= 8ull * resident) {
+        // few cameras for a large grid: most of its CTAs would find an empty
+        // cell, so list the occupied cells and run persistent CTAs over their
+        // tiles only (list and count in stream-ordered scratch)
+        grid = dim3(resident);
+        if ((e = cudaMallocAsync(&cells, 4ull * (n_cells + 1), st)) != cudaSuccess) {
+            rc = cuda_fail(e, "render_native: cell list");
+        } else {
+            a.cell_list = cells;
+            a.cell_count = cells + n_cells;
+            { rlfc::TraceScope trace_("list_cells_kernel", st); list_cells_kernel<<<1, kListThreads, 0, st>>>(a, n_cells, cells, cells + n_cells); }
+        }
+    }
+    if (rc == RLFC_OK && first) {
         uint8_t *needed = static_cast<uint8_t *>(scratch);
         uint32_t *slot_of = reinterpret_cast<uint32_t *>(needed + mask_bytes);
         uint32_t *decoded = reinterpret_cast<uint32_t *>(needed + mask_bytes + slot_bytes);
-        int rc = RLFC_OK;
         if ((e = cudaMemsetAsync(needed, 0, mask_bytes, st)) != cudaSuccess)
             rc = cuda_fail(e, "render: clearing the view mask");
         if (rc == RLFC_OK) {
@@ -851,27 +871,19 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
             { rlfc::TraceScope trace_("assign_slots_kernel", st); assign_slots_kernel<<<1, kListThreads, 0, st>>>(needed, a.sv.n_views, slot_of); }
             rc = launch_decode_packed(s, decoded, needed, slot_of, st);
         }
-        if (rc == RLFC_OK) {
-            a.decoded = decoded;
-            a.slot_of = slot_of;
-            { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
-            e = cudaGetLastError();
-            if (e != cudaSuccess)
-                rc = cuda_fail(e, "render_native launch");
-        }
-        cudaFreeAsync(scratch, st);
-        if (cells)
-            cudaFreeAsync(cells, st);
-        return rc;
+        a.decoded = decoded;
+        a.slot_of = slot_of;
     }
-    cudaGetLastError();   // a failed stream-ordered allocation only selects the other path
-    { rlfc::TraceScope trace_("render_native_kernel", st); render_native_kernel<<<grid, kThreads, kSmemBytes, st>>>(a); }
-    e = cudaGetLastError();
+    if (rc == RLFC_OK) {
+        { rlfc::TraceScope trace_("render_native_kernel", st); kern<<<grid, kThreads, smem, st>>>(a); }
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            rc = cuda_fail(e, "render_native launch");
+    }
+    if (scratch)
+        cudaFreeAsync(scratch, st);
     if (cells)
         cudaFreeAsync(cells, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "render_native launch");
-    return RLFC_OK;
+    return rc;
 }
 
 }  // namespace rlfc
