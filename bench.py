@@ -45,8 +45,8 @@ UNIT = "Mpix/s"
 # kernel); a kernel missing here reports null
 TRAFFIC_PER_LAUNCH = {
     # render_native_kernel, first timed step of `bench.py --steps 2 --warmup 1` (ncu one-pass
-    # dram__bytes_read.sum 85.90 MB + dram__bytes_write.sum 3.08 GB)
-    ("plain", 4, 1000, "render_native_kernel"): 85_900_000 + 3_080_000_000,
+    # dram__bytes_read.sum 86.56 MB + dram__bytes_write.sum 3.09 GB)
+    ("plain", 4, 1000, "render_native_kernel"): 86_560_000 + 3_090_000_000,
 }
 
 # smsp__inst_executed.sum of one launch (warp instructions), from the same kind
@@ -54,9 +54,9 @@ TRAFFIC_PER_LAUNCH = {
 # on `bench.py --steps 2 --warmup 1`); the kernels are integer and
 # conversion work bound by instruction issue more than by DRAM
 INSTR_PER_LAUNCH = {
-    ("plain", 4, 1000, "render_native_kernel"): 1_081_018_112,
+    ("plain", 4, 1000, "render_native_kernel"): 1_072_146_688,
     ("plain", 4, 1000, "decode_all_kernel"): 70_592_100,
-    ("plain", 4, 1000, "decode_all_kernel<packed>"): 76_710_223,
+    ("plain", 4, 1000, "decode_all_kernel<packed>"): 76_719_432,
 }
 # issue peak: 152 SMs x 4 schedulers x one warp instruction per cycle at the
 # 2070 MHz maximum SM clock
