@@ -410,8 +410,11 @@ RLFC_API int rlfc_encode_ex(const rlfc_enc_params *p, const uint8_t *d_rgb, cons
  * variant of rlfc_encode with byte-identical output.
  *
  * It calls no cudaMalloc, cudaFree or other device-allocating routine.  Its
- * device scratch is one array of 32 MiB compiled into the library, which a
- * device holds from the first call on that device until the process exits.
+ * device scratch is one array of 32 MiB compiled into the library.  Under
+ * lazy module loading (the CUDA default) a device holds it from the first
+ * call on that device until the process exits; with
+ * CUDA_MODULE_LOADING=EAGER every context that loads the library holds it
+ * from its creation.
  * Light fields whose encoder scratch exceeds 32 MiB (roughly up to 9 x 9
  * views of 128 x 128, depending on the tree) are rejected with RLFC_E_RANGE
  * before any work is enqueued; use rlfc_encode for those.
@@ -421,9 +424,12 @@ RLFC_API int rlfc_encode_ex(const rlfc_enc_params *p, const uint8_t *d_rgb, cons
  * size and host_out the stream; if the buffer is too small the call returns
  * RLFC_E_RANGE with *nbytes set to the size needed.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and leaves its
+ * Every call looks up the array's device address (cudaGetSymbolAddress) in
+ * the current context, so a device reset between calls is harmless; under
+ * lazy loading the first call on a device also loads the array's module.
+ * The encoder carves its buffers from the first bytes of the array, at most
+ * the bound that the size check computed, and fails with RLFC_E_CUDA rather
+ * than use more.  Every call shares the one array and leaves its
  * contents behind (the words that must start at zero are cleared on every
  * call), so calls that overlap on the GPU, from several host threads or
  * streams, race and must be serialised by the caller.  The call synchronises

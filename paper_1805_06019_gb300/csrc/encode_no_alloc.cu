@@ -8,13 +8,15 @@
 // cudaFree can cause.  This entry point serves them for light fields whose
 // encoder scratch fits in kScratchBytes.
 //
-// The array lives in this translation unit only, so its module (and its
-// kScratchBytes of device memory) is loaded on a device the first time this
-// entry point runs there, and then held until the process exits.
+// The array lives in this translation unit only.  Under lazy module loading
+// (the CUDA default since 12.2) its module, and with it kScratchBytes of
+// device memory, is loaded on a device the first time this entry point runs
+// there and then held until the process exits; with CUDA_MODULE_LOADING=EAGER
+// every context that loads the library reserves the array at creation, even
+// one that only decodes or renders.
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,35 +26,21 @@ namespace rlfc {
 namespace {
 
 constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_encode_scratch[kScratchBytes];
 
-std::mutex g_mutex;
-uint8_t *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  Host code may
+// Device address of the scratch array in the current context.  Host code may
 // not use the array's name as a device pointer, so the address is looked up
-// once per device with that device current.
+// with the device current, on every call: it allocates nothing and costs
+// little next to the encode, and a cached address would go stale if the
+// caller reset the device or the primary context was created again.
 int scratch_on_current_device(uint8_t **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_encode_scratch);
     if (e != cudaSuccess)
-        return cuda_fail(e, "no-alloc encoder: current device");
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("no-alloc encoder: device index out of range");
-        return RLFC_E_RANGE;
-    }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_encode_scratch);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "no-alloc encoder: scratch address");
-        g_scratch_addr[dev] = static_cast<uint8_t *>(ptr);
-    }
-    *out = g_scratch_addr[dev];
+        return cuda_fail(e, "no-alloc encoder: scratch address");
+    *out = static_cast<uint8_t *>(ptr);
     return RLFC_OK;
 }
 
@@ -86,7 +74,10 @@ extern "C" RLFC_API int rlfc_encode_no_alloc(const rlfc_enc_params *p, const uin
         return rc;
     try {
         std::vector<uint8_t> out;
-        rc = encode_gpu(p, d_rgb, (cudaStream_t)cuda_stream, out, scratch, kScratchBytes);
+        // the buffers are carved from the first `need` bytes only, so an
+        // encode that would use more than its bound fails instead of
+        // reaching past what the size check above admitted
+        rc = encode_gpu(p, d_rgb, (cudaStream_t)cuda_stream, out, scratch, need);
         if (rc != RLFC_OK)
             return rc;
         *nbytes = out.size();

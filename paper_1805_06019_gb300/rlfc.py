@@ -16,6 +16,7 @@ import torch
 from .buildlib import LIB
 
 RLFC_OK = 0
+RLFC_E_RANGE = 6   # a size beyond what the call supports (include/rlfc.h)
 REQ_OK, REQ_BAD_VIEW, REQ_BAD_LOCATION = 0, 1, 2
 
 
@@ -447,8 +448,14 @@ def encode_no_alloc(rgb: torch.Tensor, U: int, V: int, L: int, c, tau_p: int = 0
         p.c[l] = int(c[l])
     p.tau_p, p.tau_b, p.q = int(tau_p), int(tau_b), int(q)
     cap = int(capacity) if capacity is not None else 4 * rgb.numel() + (1 << 16)
-    buf = ctypes.create_string_buffer(cap)
-    n = ctypes.c_size_t()
-    _check(lib().rlfc_encode_no_alloc(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")),
-                                      _stream_handle(stream), buf, cap, ctypes.byref(n)))
-    return buf.raw[: n.value]
+    for _ in range(2):
+        buf = ctypes.create_string_buffer(max(cap, 1))
+        n = ctypes.c_size_t()
+        rc = lib().rlfc_encode_no_alloc(ctypes.byref(p), ctypes.c_void_p(_dev(rgb, torch.uint8, "rgb")),
+                                        _stream_handle(stream), buf, cap, ctypes.byref(n))
+        if rc == RLFC_E_RANGE and n.value > cap:
+            cap = n.value   # the stream did not fit the host buffer: its size is known now
+            continue
+        _check(rc)
+        return buf.raw[: n.value]
+    _check(rc)

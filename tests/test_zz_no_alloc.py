@@ -1,9 +1,12 @@
 """rlfc_encode_no_alloc, the encoder entry point for callers that cannot
 allocate device memory (its scratch is the library's fixed 32 MiB array),
-checked through the C ABI against rlfc_encode: the streams must be
-byte-identical, as every encoder test requires, over several calls in a row
-that reuse the shared array.  This file runs last so that a failure here
-cannot stop the rest of the GPU suite; it also passes on its own."""
+checked through the C ABI against the oracle's encoder and against
+rlfc_encode: the streams must be byte-identical, as every encoder test
+requires, over several calls in a row that reuse the shared array.  One case
+sits just under the 32 MiB limit: the entry point carves the encoder's
+buffers from no more than the scratch bound it computed, so an under-counted
+bound fails that case.  This file runs last so that a failure here cannot
+stop the rest of the GPU suite; it also passes on its own."""
 import ctypes
 
 import numpy as np
@@ -11,6 +14,7 @@ import pytest
 import torch
 
 import lf_synth
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -49,15 +53,19 @@ CASES = [
     (5, 5, 64, 64, 2, [0, 5], 2, 32, 0),
     (6, 5, 30, 21, 3, [0, 2, 3], 3, 40, 0),
     (5, 5, 20, 16, 3, [0, 2, 3], 0, 0, 2),
+    # scratch bound 32 836 608 bytes, 97.9 % of the array (9 x 9 x 184^2
+    # would need 34 312 192 and is rejected)
+    (9, 9, 180, 180, 3, [0, 3, 3], 4, 64, 0),
 ]
 
 
-def test_calls_in_a_row_match_the_allocating_encoder(rl):
+def test_calls_in_a_row_match_the_oracle_and_the_allocating_encoder(rl):
     inputs = []
     for i, (U, V, W, H, L, c, tp, tb, q) in enumerate(CASES):
         lf = lf_synth.make_lightfield(U, V, W, H, [0.0, 0.5, 1.5], 1.0, preset_id=200 + i)
         d = torch.from_numpy(lf).cuda()
-        want = rl.encode(d, U, V, L, c, tau_p=tp, tau_b=tb, q=q)
+        want = oracle.encode(lf, U, V, B=4, L=L, c=c, tau_p=tp, tau_b=tb, q=q)
+        assert rl.encode(d, U, V, L, c, tau_p=tp, tau_b=tb, q=q) == want
         inputs.append((d, _params(rl, U, V, W, H, L, c, tp, tb, q), want))
     # two passes over differently shaped light fields: the shared array must
     # carry nothing from one call into the next
@@ -85,3 +93,13 @@ def test_small_output_buffer_reports_the_size_needed(rl):
     rc, _, n = _no_alloc(rl, _params(rl, U, V, W, H, L, c, tp, tb, q), d, 16)
     assert rc == E_RANGE and n == len(want)
     assert np.frombuffer(want[:4], dtype=np.uint8).tolist() == list(b"RLFC")
+
+
+def test_binding_retries_with_the_size_the_call_reports(rl):
+    U, V, W, H, L, c, tp, tb, q = CASES[1]
+    lf = lf_synth.make_lightfield(U, V, W, H, [0.0, 0.5, 1.5], 1.0, preset_id=201)
+    want = oracle.encode(lf, U, V, B=4, L=L, c=c, tau_p=tp, tau_b=tb, q=q)
+    d = torch.from_numpy(lf).cuda()
+    # a host buffer far too small: the first call reports the stream size,
+    # the binding calls again with a buffer of that size
+    assert rl.encode_no_alloc(d, U, V, L, c, tau_p=tp, tau_b=tb, q=q, capacity=8) == want
