@@ -123,7 +123,9 @@ RLFC_API int rlfc_load_stream(const void *host_bytes, size_t nbytes, void *cuda_
 /* Shape and sizes of a loaded stream. */
 RLFC_API int rlfc_stream_info(const rlfc_stream *s, rlfc_info *out);
 
-/* Release a loaded stream and its device memory (after its work finished). */
+/* Release a loaded stream and its device memory.  It first waits for the
+ * stream's device to finish all queued work (cudaDeviceSynchronize), so work
+ * that reads the stream may still be in flight when it is called. */
 RLFC_API void rlfc_free_stream(rlfc_stream *s);
 
 /*
@@ -253,7 +255,8 @@ RLFC_API int rlfc_batch_autotune(rlfc_batch *b, const uint32_t *d_view, const ui
                                  uint8_t *d_out, uint8_t *d_status, void *cuda_stream,
                                  rlfc_batch_config *chosen);
 
-/* Release a batch object (after its work finished). */
+/* Release a batch object.  Like rlfc_free_stream it first waits for the
+ * device to finish its queued work. */
 RLFC_API void rlfc_batch_free(rlfc_batch *b);
 
 /*

@@ -759,6 +759,8 @@ RLFC_API void rlfc_batch_free(rlfc_batch *b)
     if (!b)
         return;
     rlfc::DeviceGuard g(b->device);
+    // a decode still in flight may use the batch's buffers: let the device finish first
+    cudaDeviceSynchronize();
     rlfc::drop_graph(b);
     if (b->cap)
         cudaStreamDestroy(b->cap);

@@ -412,6 +412,9 @@ void rlfc_free_stream(rlfc_stream *s)
     if (!s)
         return;
     DeviceGuard g(s->device);
+    // kernels still in flight may read the stream (a caller that drops its
+    // handle right after an asynchronous call): let the device finish first
+    cudaDeviceSynchronize();
     free_device(s);
     delete s;
 }

@@ -47,6 +47,14 @@ CASES = [
 _cache = {}
 
 
+def _mismatch(got, ref):
+    """Where two decoded light fields [views, H, W, 3] differ: the count of
+    differing pixels and the first blocks (view, block row, block column)."""
+    bad = np.argwhere((got != ref).any(-1))
+    blocks = sorted({(int(v), int(y) // 4, int(x) // 4) for v, y, x in bad})
+    return {"pixels": len(bad), "blocks": len(blocks), "first": blocks[:12]}
+
+
 def _case(name):
     if name not in _cache:
         _, U, V, W, H, L, c, tp, tb, q = next(x for x in CASES if x[0] == name)
@@ -258,7 +266,7 @@ def test_plain_full_decode_and_encode(rlfc, plain):
         assert rlfc.encode(d_lf, p["U"], p["V"], p["L"], p["c"], tau_p=tau, tau_b=16 * tau) == data
         ref = oracle.Stream(data).decode_all(nthreads=8)
         got = rlfc.Stream(data).decode_all().cpu().numpy()
-        assert np.array_equal(got, ref), tau
+        assert np.array_equal(got, ref), (tau, _mismatch(got, ref))
 
 
 def test_plain_render_1000_views_sampled(rlfc, plain):
