@@ -13,7 +13,7 @@ namespace rlfc {
 
 constexpr int kMaxLevels = 8;
 constexpr uint32_t kDecodeStrip = 8;   // block locations per CTA of the full decode
-constexpr int kPadWords = 8;   // zero words after the records (bit-reader over-read)
+constexpr int kPadWords = 16;  // zero words after the records (decoder and staging over-read)
 
 // Per BFS position: level (bits 0..3), parent reference (bits 4..17: the top
 // RKV index when the parent is the top level, else the parent's BFS
