@@ -47,6 +47,9 @@ TRAFFIC_PER_LAUNCH = {
     # render_native_kernel, first timed step of `bench.py --steps 2 --warmup 1` (ncu one-pass
     # dram__bytes_read.sum 86.56 MB + dram__bytes_write.sum 3.09 GB)
     ("plain", 4, 1000, "render_native_kernel"): 86_560_000 + 3_090_000_000,
+    # decode_all_kernel on the 17x17x1024^2 light field at tau 4 (ncu --set full, one launch:
+    # dram__bytes_read.sum 99.21 MB + dram__bytes_write.sum 859.85 MB)
+    ("batching", 4, 0, "decode_all_kernel"): 99_212_544 + 859_851_520,
 }
 
 # smsp__inst_executed.sum of one launch (warp instructions), from the same kind
@@ -55,8 +58,7 @@ TRAFFIC_PER_LAUNCH = {
 # conversion work bound by instruction issue more than by DRAM
 INSTR_PER_LAUNCH = {
     ("plain", 4, 1000, "render_native_kernel"): 1_072_146_688,
-    ("plain", 4, 1000, "decode_all_kernel"): 70_592_100,
-    ("plain", 4, 1000, "decode_all_kernel<packed>"): 76_719_432,
+    ("batching", 4, 0, "decode_all_kernel"): 424_489_659,
 }
 # issue peak: 152 SMs x 4 schedulers x one warp instruction per cycle at the
 # 2070 MHz maximum SM clock
@@ -187,12 +189,14 @@ def _kernel_bytes(info, stream_read, n_views_lf, n_needed, n_render, out_w, out_
     return {
         # compressed stream read once, RGB8 written
         "decode_all_kernel": stream_read + 3 * px_view * n_views_lf,
-        # the views the renderer needs, as one 32-bit RGB word per pixel
-        "decode_all_kernel<packed>": stream_read + 4 * px_view * n_needed,
+        # the renderer's decode of the views it samples: the stream read (the
+        # packed views it writes are the renderer's own intermediate)
+        "decode_all_kernel<packed>": stream_read,
         # camera table read, one mask byte per view written
         "mark_needed_kernel": 12 * n_render + n_views_lf,
-        # decoded neighbour views read once, float RGB written
-        "render_native_kernel": 4 * px_view * n_needed + 12 * out_px,
+        # float RGB written (the decoded views it reads are the renderer's
+        # own intermediate, not bytes the method must move)
+        "render_native_kernel": 12 * out_px,
         "render_tiled_kernel": stream_read + 12 * out_px,
         "render_direct_kernel": stream_read + 12 * out_px,
     }
@@ -216,6 +220,135 @@ def job_mpix_per_s(world, px_per_rank, ms):
     return world * px_per_rank / (ms * 1e-3) / 1e6
 
 
+DTYPE = "int decode + fp32 render"
+
+
+def _median(xs):
+    return float(np.median(np.asarray(xs, dtype=np.float64)))
+
+
+def _timed_calls(torch, fn, reps, flush, warmup=3):
+    """Per-call device times (ms) of `reps` calls of fn, each after a write
+    that flushes L2, bracketed by CUDA events on the current stream."""
+    cur = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ms = []
+    for k in range(reps):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        fn()
+        b.record(cur)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def _traced(rlfc, torch, fn, reps, flush):
+    """Per-kernel launch counts and summed durations (the library's own CUDA
+    events) over `reps` flushed calls of fn."""
+    rlfc.trace_read(reset=True)
+    rlfc.trace_enable(True)
+    for k in range(reps):
+        flush.fill_(k & 255)
+        fn()
+    torch.cuda.synchronize()
+    tr = rlfc.trace_read(reset=True)
+    rlfc.trace_enable(False)
+    return tr
+
+
+def _extra_parts(rlfc, torch, args, p, tau, st, out_lf, flush, peak, world):
+    """Beside the step: the plain decode at the other thresholds of the sweep,
+    the full decode of the 17 x 17 x 1024^2 light field (the bandwidth test of
+    the decoder) and 10^6 random block requests on it, batched and as one warp
+    per request.  Device times are medians over at least 20 flushed calls."""
+    reps = max(args.steps, 20)
+    U, V = p["U"], p["V"]
+    out = {}
+    px_lf = U * V * p["W"] * p["H"]
+    if not args.no_sweep:
+        d_lf = lf_synth.make_lightfield_torch(U, V, p["W"], p["H"], p["disparities"], p["sigma"], p["id"],
+                                              p.get("contrast", False))
+        for t in p.get("taus", [tau]):
+            if t == tau:
+                continue
+            s_t = rlfc.Stream(rlfc.encode(d_lf, U, V, p["L"], p["c"], tau_p=t, tau_b=16 * t))
+            b_t, _, _ = _algorithmic_bytes(s_t.info, U * V, 0, 0, 0)
+            ms = max_over_ranks([_median(_timed_calls(torch, lambda: s_t.decode_all(out_lf), reps, flush))], world,
+                                "cuda")[0]
+            out[f"decode_all_tau{t}"] = {"ms": ms, "mpix_s": px_lf / (ms * 1e-3) / 1e6, "algorithmic_bytes": b_t,
+                                         "gbs": b_t / (ms * 1e-3) / 1e9, "hbm_frac": b_t / (ms * 1e-3) / 1e9 / peak,
+                                         "stream_bytes": int(s_t.info.stream_bytes)}
+            s_t.close()
+        del d_lf
+    roof_dec = None
+    if not args.no_batching:
+        pb = lf_synth.PRESETS["batching"]
+        t0 = time.time()
+        d_b = lf_synth.preset_lightfield_torch("batching")
+        torch.cuda.synchronize()
+        t_synth = time.time() - t0
+        tb = pb["taus"][0]
+        s_b = rlfc.Stream(rlfc.encode(d_b, pb["U"], pb["V"], pb["L"], pb["c"], tau_p=tb, tau_b=16 * tb))
+        del d_b
+        ib = s_b.info
+        nv = pb["U"] * pb["V"]
+        px_b = nv * pb["W"] * pb["H"]
+        lf_b = torch.empty((nv, pb["H"], pb["W"], 3), dtype=torch.uint8, device="cuda")
+        ms_b = _timed_calls(torch, lambda: s_b.decode_all(lf_b), reps, flush)
+        tr = _traced(rlfc, torch, lambda: s_b.decode_all(lf_b), reps, flush)
+        alg_b, _, _ = _algorithmic_bytes(ib, nv, 0, 0, 0)
+        med_b = max_over_ranks([_median(ms_b)], world, "cuda")[0]
+        k_launch, k_tot = tr.get("decode_all_kernel", (1, med_b))
+        k_ms = max_over_ranks([k_tot / max(k_launch, 1)], world, "cuda")[0]
+        out["decode_all_17x17x1024"] = {
+            "ms": med_b, "mpix_s": px_b / (med_b * 1e-3) / 1e6, "algorithmic_bytes": alg_b,
+            "gbs": alg_b / (med_b * 1e-3) / 1e9, "hbm_frac": alg_b / (med_b * 1e-3) / 1e9 / peak,
+            "kernel_ms": k_ms, "stream_bytes": int(ib.stream_bytes), "synth_s": t_synth,
+            "workload": f"{pb['U']}x{pb['V']} views of {pb['W']}x{pb['H']}, 8 planes -3..3, contrast-modulated, "
+                        f"3-level tree {tuple(pb['c'][1:])}, tau {tb}: every block of every view"}
+        roof_dec = {"bound": "hbm", "kernel": "decode_all_kernel", "workload": "17x17x1024^2 full decode",
+                    "achieved": alg_b / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": alg_b / (k_ms * 1e-3) / 1e9 / peak, "bytes_per_launch": alg_b, "avg_launch_ms": k_ms,
+                    "traffic": TRAFFIC_PER_LAUNCH.get(("batching", tb, 0, "decode_all_kernel")),
+                    "peak_source": "measured hbm_gbs (burst copy)" if _peaks()[1] == "measured" else "fallback"}
+        instr = INSTR_PER_LAUNCH.get(("batching", tb, 0, "decode_all_kernel"))
+        if instr is not None:
+            roof_dec["issue"] = {"achieved": instr / (k_ms * 1e-3), "peak": ISSUE_PEAK, "unit": "warp instructions/s",
+                                 "frac": instr / (k_ms * 1e-3) / ISSUE_PEAK, "instructions_per_launch": instr}
+        # 10^6 uniform random (view, location) requests
+        n = pb["n_requests"]
+        pv, pl = lf_synth.random_requests(n, nv, s_b.nloc, pb["id"])
+        views = torch.from_numpy(pv.view(np.int32)).cuda()
+        locs = torch.from_numpy(pl.view(np.int32)).cuda()
+        ref_blocks = torch.empty((n, 4, 4, 3), dtype=torch.uint8, device="cuda")
+        blocks = torch.empty((n, 4, 4, 3), dtype=torch.uint8, device="cuda")
+        per_req = max_over_ranks([_median(_timed_calls(torch, lambda: s_b.decode_blocks(views, locs, ref_blocks),
+                                                       reps, flush))], world, "cuda")[0]
+        bt = rlfc.Batch(s_b, n)
+        bt.config = dict(graph=0)
+        chosen = dict(bt.autotune(views, locs, blocks))
+        bt.config = dict(graph=1)
+        chosen["graph"] = 1
+        blocks.zero_()
+        g_ms = max_over_ranks([_median(_timed_calls(torch, lambda: bt.decode(views, locs, blocks), reps, flush))],
+                              world, "cuda")[0]
+        same = bool(torch.equal(blocks, ref_blocks))
+        out["batched_requests_1e6"] = {
+            "ms": g_ms, "requests_per_s": n / (g_ms * 1e-3), "mpix_s": 16 * n / (g_ms * 1e-3) / 1e6,
+            "config": chosen, "identical_to_per_request": same,
+            "note": "persistent binned kernel, autotuned, replayed as a CUDA graph"}
+        out["per_request_1e6"] = {"ms": per_req, "requests_per_s": n / (per_req * 1e-3),
+                                  "mpix_s": 16 * n / (per_req * 1e-3) / 1e6, "note": "one warp per request"}
+        out["batched_speedup_vs_per_request"] = per_req / g_ms
+        bt.close()
+        s_b.close()
+        del lf_b, views, locs, blocks, ref_blocks
+    return out, roof_dec
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -230,9 +363,10 @@ def run_ours(args):
 
     p, n_render, out_w, out_h, tau = _workload(args)
     U, V = p["U"], p["V"]
-    lf = lf_synth.preset_lightfield(args_config_name(p))
-    d_lf = torch.from_numpy(lf).cuda()
+    d_lf = lf_synth.make_lightfield_torch(U, V, p["W"], p["H"], p["disparities"], p["sigma"], p["id"],
+                                          p.get("contrast", False))
     data = rlfc.encode(d_lf, U, V, p["L"], p["c"], tau_p=tau, tau_b=16 * tau)
+    lf = d_lf.cpu().numpy() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     del d_lf
     st = rlfc.Stream(data)
     cams = lf_synth.random_views(n_render, U, V, p["id"], d_choices=p["disparities"])
@@ -281,6 +415,7 @@ def run_ours(args):
     rlfc.trace_enable(False)
     t_dec = [a.elapsed_time(b) for a, b, _ in evs]
     t_ren = [b.elapsed_time(c) for _, b, c in evs]
+    t_step = [a.elapsed_time(c) for a, _, c in evs]
     # the same calls back to back without the flush: warm-L2 figures beside
     # the flushed ones (the compressed stream stays in L2 between calls)
     wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -293,11 +428,10 @@ def run_ours(args):
         st.render(uv, disp, out_w, out_h, out_views)
         c.record(cur)
     torch.cuda.synchronize()
-    dec_warm, ren_warm = max_over_ranks([sum(a.elapsed_time(b) for a, b, _ in wev) / args.steps,
-                                         sum(b.elapsed_time(c) for _, b, c in wev) / args.steps], world, "cuda")
-    step_ms = sum(t_dec) / args.steps + sum(t_ren) / args.steps
-    step_ms, dec_ms, ren_ms = max_over_ranks([step_ms, sum(t_dec) / args.steps, sum(t_ren) / args.steps],
-                                             world, "cuda")
+    dec_warm, ren_warm = max_over_ranks([_median([a.elapsed_time(b) for a, b, _ in wev]),
+                                         _median([b.elapsed_time(c) for _, b, c in wev])], world, "cuda")
+    step_ms, dec_ms, ren_ms, step_mean = max_over_ranks(
+        [_median(t_step), _median(t_dec), _median(t_ren), float(np.mean(t_step))], world, "cuda")
 
     info = st.info
     px_lf = U * V * p["W"] * p["H"]
@@ -309,7 +443,8 @@ def run_ours(args):
     ren_gbs = b_ren / (ren_ms * 1e-3) / 1e9
     parts = {
         "decode_all": {"ms": dec_ms, "mpix_s": px_lf / (dec_ms * 1e-3) / 1e6, "algorithmic_bytes": b_dec,
-                       "gbs": dec_gbs, "hbm_frac": dec_gbs / peak, "ms_warm": dec_warm},
+                       "gbs": dec_gbs, "hbm_frac": dec_gbs / peak, "ms_warm": dec_warm,
+                       "note": f"the step's light field at tau {tau}; the stream stays in L2 across calls"},
         "render": {"ms": ren_ms, "ms_warm": ren_warm, "views_per_s": n_render / (ren_ms * 1e-3),
                    "mpix_s": px_render / (ren_ms * 1e-3) / 1e6,
                    "algorithmic_bytes": b_ren, "gbs": ren_gbs, "hbm_frac": ren_gbs / peak},
@@ -358,7 +493,7 @@ def run_ours(args):
         h_lf = [torch.empty(out_lf.shape, dtype=torch.uint8).pin_memory() for _ in range(2)]
         h_views = [torch.empty(out_views.shape, dtype=vdt).pin_memory() for _ in range(2)]
         copy_st = torch.cuda.Stream()
-        e_steps = min(args.steps, 5)
+        e_steps = max(args.steps, 5)
         done = [None, None]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -388,7 +523,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(h_lf[0].numel() + h_views[0].numel() * h_views[0].element_size()),
                 "steps": e_steps,
                 "note": "downloads of step k overlap step k+1 on a copy stream; the device-to-host link "
-                        "(about 193 GB/s measured on GB300 hosts) bounds it"}
+                        "bounds it"}
 
     e2e = e2e_u8 = None
     if not args.no_e2e:
@@ -397,35 +532,29 @@ def run_ours(args):
         e2e_u8["note"] = "the same step with 8-bit views (rlfc_render_views_u8), " + e2e_u8["note"]
     # the render call with 8-bit output, device-timed like the step
     views8 = torch.empty(out_views.shape, dtype=torch.uint8, device="cuda")
-    st.render(uv, disp, out_w, out_h, views8)
-    r8 = []
-    for k in range(args.steps):
-        flush.fill_(k & 255)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(cur)
-        st.render(uv, disp, out_w, out_h, views8)
-        b.record(cur)
-        torch.cuda.synchronize()
-        r8.append(a.elapsed_time(b))
+    r8_ms = max_over_ranks([_median(_timed_calls(torch, lambda: st.render(uv, disp, out_w, out_h, views8),
+                                                 max(args.steps, 20), flush))], world, "cuda")[0]
     del views8
-    r8_ms = max_over_ranks([sum(r8) / len(r8)], world, "cuda")[0]
     parts["render_u8"] = {"ms": r8_ms, "views_per_s": n_render / (r8_ms * 1e-3),
                           "mpix_s": px_render / (r8_ms * 1e-3) / 1e6,
                           "note": "rlfc_render_views_u8: the same views as 8-bit RGB (3 B/px written)"}
+    extra, roof_dec = _extra_parts(rlfc, torch, args, p, tau, st, out_lf, flush, peak, world)
+    parts.update(extra)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if lf is not None:
         cpu = cpu_baseline(p, lf, tau, n_render, out_w, out_h, cams, sample_views=args.cpu_sample_views)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": _config_json(p, n_render, out_w, out_h, tau,
-                                       {"stream_bytes": int(info.stream_bytes), "parallelism": f"replicas{world}"}),
-                "parts": parts, "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "e2e_u8": e2e_u8,
-                "gpu_launches": gpu_launches, "clocks": clk}
+                "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
+                "config": _config_json(p, n_render, out_w, out_h, tau, {"parallelism": f"replicas{world}"}),
+                "timing": {"ms_per_step_median": step_ms, "ms_per_step_mean": step_mean,
+                           "steps_timed": args.steps, "l2": "flushed by a 256 MiB write before every timed step"},
+                "parts": parts, "kernels": kernels, "roofline": roof, "roofline_decode": roof_dec,
+                "cpu_baseline": cpu, "e2e": e2e, "e2e_u8": e2e_u8,
+                "gpu_launches": gpu_launches, "clocks": clk, "stream_bytes": int(info.stream_bytes)}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -483,6 +612,9 @@ def cpu_baseline(p, lf, tau, n_render, out_w, out_h, cams, sample_views=50):
 
 
 def run_reference(args):
+    """The oracle (the plain C restatement of the paper) as the reference arm:
+    every step is the whole workload on the host cores, the decode of every
+    view and all renders, nothing extrapolated."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
@@ -491,22 +623,23 @@ def run_reference(args):
     lf = lf_synth.preset_lightfield(args_config_name(p))
     cams = lf_synth.random_views(n_render, p["U"], p["V"], p["id"], d_choices=p["disparities"])
     ncpu = os.cpu_count() or 1
-    k_views = min(n_render, 8 * ncpu)
     ost = _oracle_stream(p, lf, tau)
     for _ in range(args.warmup):
-        _oracle_sample(p, ost, n_render, out_w, out_h, cams, k_views, threads=ncpu)
-    steps = [_oracle_sample(p, ost, n_render, out_w, out_h, cams, k_views, threads=ncpu)
+        _oracle_sample(p, ost, n_render, out_w, out_h, cams, n_render, threads=ncpu)
+    steps = [_oracle_sample(p, ost, n_render, out_w, out_h, cams, n_render, threads=ncpu)
              for _ in range(args.steps)]
-    step_s = float(np.mean([s[1] for s in steps]))
+    step_s = _median([s[1] for s in steps])
     px = p["U"] * p["V"] * p["W"] * p["H"] + n_render * out_w * out_h
     value = px / step_s / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": _config_json(p, n_render, out_w, out_h, tau),
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
+            "config": _config_json(p, n_render, out_w, out_h, tau, {"parallelism": f"replicas{world}"}),
+            "timing": {"ms_per_step_median": step_s * 1e3, "ms_per_step_mean": float(np.mean([s[1] for s in steps])) * 1e3,
+                       "steps_timed": args.steps},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": ncpu,
-                             "sample": f"per step: oracle decode of all {p['U'] * p['V']} views plus {k_views} "
-                                       f"renders ({ncpu} threads), render time scaled to {n_render} views"},
+                             "sample": f"per step: oracle decode of all {p['U'] * p['V']} views plus all {n_render} "
+                                       f"renders ({ncpu} threads), median over {args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -647,7 +780,7 @@ def run_batching(args):
     px = 16 * n
     line = {"metric": METRIC, "value": px / (graph_ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int decode", "data": "synthetic",
             "config": {"workload": f"batching: {U}x{V} views of {p['W']}x{p['H']} RGB, 8 planes -3..3, "
                                    f"contrast-modulated, 3-level tree {tuple(p['c'][1:])}, 4x4 blocks, tau {tau}; "
                                    f"{n} uniform random (view, location) requests per launch",
@@ -857,7 +990,7 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="plain", choices=["plain", "tiny"])
@@ -865,6 +998,9 @@ def main():
     ap.add_argument("--n-views", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the other thresholds' decode parts")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the 17x17x1024^2 full-decode and 10^6-request parts")
     ap.add_argument("--cpu-sample-views", type=int, default=400)
     ap.add_argument("--workload", choices=["step", "batching", "serving", "learned"], default="step",
                     help="step: decode-all + render (default); batching: random block requests; "
