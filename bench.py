@@ -540,6 +540,9 @@ def run_ours(args):
                           "note": "rlfc_render_views_u8: the same views as 8-bit RGB (3 B/px written)"}
     extra, roof_dec = _extra_parts(rlfc, torch, args, p, tau, st, out_lf, flush, peak, world)
     parts.update(extra)
+    if not args.no_serving and world == 1:
+        parts["serving_vs_per_request"] = serving_compare(rlfc, torch, [float(r) for r in args.compare_rates.split(",")],
+                                                          args.compare_seconds)
 
     cpu = None
     if lf is not None:
@@ -811,6 +814,86 @@ def run_batching(args):
     print(json.dumps(line))
 
 
+def _serve_trace(rlfc, srv, ids, grids, pool, rate, n, preset_id, u8):
+    """Submit n requests arriving as a seeded Poisson process at `rate` to
+    srv (light field uniform over `ids`, camera and focus plane uniform), each
+    into a free pinned destination of `pool` (reused once its request has
+    completed), and wait for every completion.  Latency is submit -> view in
+    pinned host memory."""
+    arr = lf_synth.poisson_arrivals(rate, n, preset_id=preset_id)
+    lf_i, fu, fv, fd = lf_synth.serving_requests(n, len(ids), preset_id=preset_id)
+    free = {k: list(range(len(v))) for k, v in pool.items()}
+    owner = {}
+    comps, waited = [], 0
+    base = rlfc.Server.now() + 0.05
+    for i in range(n):
+        U, V, W, H, disp = grids[lf_i[i]]
+        while not free[(W, H)]:
+            waited += 1
+            for c in srv.poll():
+                comps.append(c)
+                free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
+        slot = free[(W, H)].pop()
+        while rlfc.Server.now() < base + arr[i]:
+            pass
+        t = srv.submit(ids[lf_i[i]], fu[i] * (U - 1), fv[i] * (V - 1),
+                       disp[min(int(fd[i] * len(disp)), len(disp) - 1)], pool[(W, H)][slot])
+        owner[t] = ((W, H), slot)
+        if i % 16 == 0:
+            for c in srv.poll():
+                comps.append(c)
+                free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
+    comps += srv.poll(wait=True)
+    lat = np.array([c["t_done"] - c["t_submit"] for c in comps]) * 1e3
+    span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
+    px = sum(grids[c["lf"]][2] * grids[c["lf"]][3] for c in comps)
+    return {"format": "u8" if u8 else "f32", "rate_req_s": rate, "requests": n,
+            "ok": int(sum(c["status"] == 0 for c in comps)),
+            "views_per_s": len(comps) / span, "mpix_s": px / span / 1e6,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": float(np.mean([c["batch"] for c in comps])),
+            "client_waits_for_buffers": waited}
+
+
+def serving_compare(rlfc, torch, rates, seconds, pool_size=256):
+    """The served form against the plain per-request launch on the same GPU:
+    the three 5 x 5 x 256^2 serving light fields (tau 2 / 4 / 8) resident, the
+    same seeded Poisson trace of 8-bit 256^2 view requests at each rate, through
+    the server configured two ways: one render call per request on one stream
+    (calls queue in the stream), and continuous batching (up to 64 views per
+    call, four streams, one call in flight per stream)."""
+    streams, grids = [], []
+    for name, tau in lf_synth.SERVING_FLEET:
+        if name != "serving_small":
+            continue
+        p = lf_synth.PRESETS[name]
+        d_lf = lf_synth.preset_lightfield_torch(name)
+        streams.append(rlfc.Stream(rlfc.encode(d_lf, p["U"], p["V"], p["L"], p["c"], tau_p=tau, tau_b=16 * tau)))
+        grids.append((p["U"], p["V"], p["W"], p["H"], p["disparities"]))
+        del d_lf
+    W, H = grids[0][2], grids[0][3]
+    pool = {(W, H): [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(pool_size)]}
+    forms = {"per_request": dict(n_streams=1, max_batch=1, max_inflight=64),
+             "served": dict(n_streams=4, max_batch=64, max_inflight=1)}
+    out = {}
+    for form, cfg in forms.items():
+        srv = rlfc.Server(memory_budget=1 << 30, **cfg)
+        ids = [srv.add(st) for st in streams]
+        # a short warm-up trace, then the measured rates
+        _serve_trace(rlfc, srv, ids, grids, pool, 2000.0, 200, 40, True)
+        out[form] = {"config": cfg, "rates": [_serve_trace(rlfc, srv, ids, grids, pool, r, max(int(r * seconds), 200),
+                                                           41 + ri, True) for ri, r in enumerate(rates)]}
+        srv.close()
+    for st in streams:
+        st.close()
+    sat = {f: max(x["views_per_s"] for x in v["rates"]) for f, v in out.items()}
+    out["max_views_per_s"] = sat
+    out["served_over_per_request_at_saturation"] = sat["served"] / sat["per_request"]
+    out["workload"] = ("3 resident 5x5x256^2 light fields (tau 2/4/8), 8-bit 256^2 view requests, the same seeded "
+                       f"Poisson trace per rate ({seconds} s each); latency = submit to view in pinned host memory")
+    return out
+
+
 def run_serving(args):
     """Eight resident light fields (three 5x5x256^2, three 9x9x512^2, two
     17x17x1024^2), view requests at their native sizes arriving as a Poisson
@@ -852,38 +935,7 @@ def run_serving(args):
                                           .pin_memory() for _ in range(args.serve_pool)]
         pool = pools[fmt]
         n = max(int(rate * args.serve_seconds), 50)
-        arr = lf_synth.poisson_arrivals(rate, n, preset_id=4 + ri)
-        lf_i, fu, fv, fd = lf_synth.serving_requests(n, len(streams), preset_id=4 + ri)
-        free = {k: list(range(len(v))) for k, v in pool.items()}
-        owner = {}
-        comps, waited = [], 0
-        base = rlfc.Server.now() + 0.05
-        for i in range(n):
-            U, V, W, H, disp = grids[lf_i[i]]
-            while not free[(W, H)]:
-                waited += 1
-                for c in srv.poll():
-                    comps.append(c)
-                    free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
-            slot = free[(W, H)].pop()
-            while rlfc.Server.now() < base + arr[i]:
-                pass
-            t = srv.submit(ids[lf_i[i]], fu[i] * (U - 1), fv[i] * (V - 1),
-                           disp[min(int(fd[i] * len(disp)), len(disp) - 1)], pool[(W, H)][slot])
-            owner[t] = ((W, H), slot)
-            if i % 16 == 0:
-                for c in srv.poll():
-                    comps.append(c)
-                    free[owner[c["ticket"]][0]].append(owner[c["ticket"]][1])
-        comps += srv.poll(wait=True)
-        lat = np.array([c["t_done"] - c["t_submit"] for c in comps]) * 1e3
-        span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
-        px = sum(grids[c["lf"]][2] * grids[c["lf"]][3] for c in comps)
-        results.append({"format": fmt, "rate_req_s": rate, "requests": n, "ok": int(sum(c["status"] == 0 for c in comps)),
-                        "views_per_s": len(comps) / span, "mpix_s": px / span / 1e6,
-                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                        "mean_batch": float(np.mean([c["batch"] for c in comps])),
-                        "client_waits_for_buffers": waited})
+        results.append(_serve_trace(rlfc, srv, ids, grids, pool, rate, n, 4 + ri, fmt == "u8"))
     srv.close()
     top = [r for r in results if r["format"] == formats[0]][-1]
     line = {"metric": METRIC, "value": top["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates), "warmup": 0,
@@ -1001,6 +1053,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the other thresholds' decode parts")
     ap.add_argument("--no-batching", action="store_true",
                     help="skip the 17x17x1024^2 full-decode and 10^6-request parts")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served vs per-request part")
+    ap.add_argument("--compare-rates", default="5000,10000,20000,40000,80000")
+    ap.add_argument("--compare-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-sample-views", type=int, default=400)
     ap.add_argument("--workload", choices=["step", "batching", "serving", "learned"], default="step",
                     help="step: decode-all + render (default); batching: random block requests; "
