@@ -696,18 +696,32 @@ __global__ void __launch_bounds__(kThreads, 3) decode_all_kernel(const Args a)
             const uint32_t excl = incl - cnt;
             const uint32_t totals = __shfl_sync(kFullMask, incl, 31);
             const uint32_t n_items = totals & 0xFFFFu, n_slots = totals >> 16;
+            // items are numbered view-major (a view's locations in order), so
+            // that lanes of the conversion below write neighbouring blocks of
+            // one output row together; slots stay location-major.  Lane v < 16:
+            // the run's locations holding an item of view ub + v, and the
+            // items of the views before it.
+            uint32_t vrow = 0;
+            for (uint32_t l = l0; l < l1; l++) {
+                const uint32_t al = __shfl_sync(kFullMask, (f0 | f1 | f2) & sel, l);
+                vrow |= ((al >> ((ub + lane) & 31u)) & 1u) << l;
+            }
+            vrow = lane < kUnit ? vrow : 0u;
+            const uint32_t vcnt = (uint32_t)__popc(vrow);
+            const uint32_t vbase = warp_inclusive_scan(vcnt, lane) - vcnt;
             // items and slots: lane = (location, position) pairs of the run
             for (uint32_t q0 = 0; q0 < (l1 - l0) * kUnit; q0 += 32) {
                 const uint32_t q = q0 + lane;
                 const uint32_t l = min(l0 + (q >> 4), (uint32_t)kNL - 1u), bit = ub + (q & 15u);
                 const uint32_t g0 = __shfl_sync(kFullMask, f0, l), g1 = __shfl_sync(kFullMask, f1, l),
                                g2 = __shfl_sync(kFullMask, f2, l), eb = __shfl_sync(kFullMask, excl, l);
+                const uint32_t vb = __shfl_sync(kFullMask, vbase, q & 15u), vr = __shfl_sync(kFullMask, vrow, q & 15u);
                 const bool valid = q < (l1 - l0) * kUnit;
                 const uint32_t m0 = valid ? g0 & sel : 0u, m1 = valid ? g1 & sel : 0u, m2 = valid ? g2 & sel : 0u;
                 const uint32_t st3 = ((m0 >> bit) & 1u) | (((m1 >> bit) & 1u) << 1) | (((m2 >> bit) & 1u) << 2);
                 if (st3) {
                     const uint32_t lt = (1u << bit) - 1u;
-                    const uint32_t item = (eb & 0xFFFFu) + __popc((m0 | m1 | m2) & lt);
+                    const uint32_t item = vb + __popc(vr & ((1u << l) - 1u));
                     uint32_t slot = (eb >> 16) + __popc(m0 & lt) + __popc(m1 & lt) + __popc(m2 & lt);
                     witems[item] = (w * 32 + bit) | (l << 14) | (st3 << 18) | (slot << 21);
                     if (st3 & 1u)

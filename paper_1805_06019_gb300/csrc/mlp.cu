@@ -187,44 +187,170 @@ __global__ void ks_features_kernel(const int16_t *resid, const uint8_t *label_in
         label_out[i] = label_in ? label_in[src] : (uint8_t)0xFF;
 }
 
-struct NetSmem {
-    float *w1t, *b1, *w2t, *b2, *w3t, *b3;   // transposed weights [in][out]
-    float *x, *h1, *h2, *z, *d2, *d1;        // one tile of activations / deltas
+// ---- BF16 tensor-core tiles -------------------------------------------------
+//
+// Every product of the network runs on the tensor pipe: mma.sync m16n8k16
+// with BF16 operands and FP32 accumulation.  The weights and the inputs are
+// BF16 values already (one term); an FP32 activation or delta is split into
+// a BF16 high part and a BF16 residual, hi + lo, which carries 16 bits of its
+// mantissa, so that a product with a weight is hi * w + lo * w (two MMAs) and
+// a product of two FP32 operands hi * hi' + hi * lo' + lo * hi' (three).  The
+// results then differ from FP32 arithmetic by a few units of 2^-16.
+//
+// Fragments (per lane, g = lane / 4, t = lane % 4): A (16 x 16, row-major)
+// holds A[g][k..k+1], A[g+8][k..k+1], A[g][k+8..k+9], A[g+8][k+8..k+9] with
+// k = 2t; B (16 x 8) holds B[2t..2t+1][g], B[2t+8..2t+9][g]; C (16 x 8)
+// holds C[g][2t..2t+1], C[g+8][2t..2t+1].  Pairs are packed low element
+// first.
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Two floats to a BF16 pair (x0 in the low half), rounded to nearest.
+__device__ __forceinline__ uint32_t pack_bf16(float x0, float x1)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+    return r;
+}
+
+// hi = bf16(x), lo = bf16(x - hi), for a pair.
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack_bf16(x0, x1);
+    lo = pack_bf16(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xFFFF0000u));
+}
+
+// Leading dimensions (floats) of the FP32 activation tiles: 4 mod 16 keeps
+// the column-wise fragment loads on distinct banks.
+constexpr int LX = NI + 4, LH = NH + 4, LZ = NO + 4;
+// Row strides (BF16 elements) of the weight copies: the row-wise fragment
+// loads fall on distinct banks.
+constexpr int LW1 = NI + 8, LW2 = NH + 8, LW3 = NH + 8, LW2T = NH + 8, LW3T = NO + 8;
+
+// A fragment of a row-major FP32 tile M[m][k] (rows m0.., columns k0..).
+template <bool kExact>
+__device__ __forceinline__ void frag_a_rows(const float *M, int ld, int m0, int k0, uint32_t hi[4], uint32_t lo[4])
+{
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float2 v = *reinterpret_cast<const float2 *>(M + (m0 + g + 8 * (q & 1)) * ld + k0 + 2 * t + 8 * (q >> 1));
+        if (kExact)
+            hi[q] = pack_bf16(v.x, v.y);
+        else
+            split2(v.x, v.y, hi[q], lo[q]);
+    }
+}
+
+// A fragment of the transpose of an FP32 tile: A[m][k] = M[k][m].
+__device__ __forceinline__ void frag_a_cols(const float *M, int ld, int m0, int k0, uint32_t hi[4], uint32_t lo[4])
+{
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int m = m0 + g + 8 * (q & 1), k = k0 + 2 * t + 8 * (q >> 1);
+        split2(M[k * ld + m], M[(k + 1) * ld + m], hi[q], lo[q]);
+    }
+}
+
+// B fragment of BF16 weights stored n-major, B[k][n] = Wb[n][k] (row stride ldw).
+__device__ __forceinline__ void frag_b_w(const uint16_t *Wb, int ldw, int n0, int k0, uint32_t b[2])
+{
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(Wb + (n0 + g) * ldw + k0);
+    b[0] = row[t];
+    b[1] = row[4 + t];
+}
+
+// B fragment of a row-major FP32 tile, B[k][n] = M[k][n].
+template <bool kExact>
+__device__ __forceinline__ void frag_b_rows(const float *M, int ld, int n0, int k0, uint32_t hi[2], uint32_t lo[2])
+{
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int k = k0 + 2 * t + 8 * q;
+        const float x0 = M[k * ld + n0 + g], x1 = M[(k + 1) * ld + n0 + g];
+        if (kExact)
+            hi[q] = pack_bf16(x0, x1);
+        else
+            split2(x0, x1, hi[q], lo[q]);
+    }
+}
+
+// C tile (16 x 8) at (m0, n0) of act(b + X W^T): X an FP32 activation tile
+// [m][K] (row stride ldx; BF16 values exactly when kXExact), W BF16 weights
+// [N][K], stored into Y (row stride ldy).
+template <int K, bool kXExact, bool kRelu>
+__device__ __forceinline__ void dense_tile(const float *X, int ldx, const uint16_t *Wb, int ldw, const float *b,
+                                           float *Y, int ldy, int m0, int n0)
+{
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t ah[4], al[4], bw[2];
+        frag_a_rows<kXExact>(X, ldx, m0, k0, ah, al);
+        frag_b_w(Wb, ldw, n0, k0, bw);
+        mma_bf16(c, ah, bw);
+        if (!kXExact)
+            mma_bf16(c, al, bw);
+    }
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3, n = n0 + 2 * t;
+    const float b0 = b[n], b1 = b[n + 1];
+    float y[4] = {c[0] + b0, c[1] + b1, c[2] + b0, c[3] + b1};
+    if (kRelu)
+        for (int q = 0; q < 4; q++)
+            y[q] = fmaxf(y[q], 0.0f);
+    *reinterpret_cast<float2 *>(Y + (m0 + g) * ldy + n) = make_float2(y[0], y[1]);
+    *reinterpret_cast<float2 *>(Y + (m0 + g + 8) * ldy + n) = make_float2(y[2], y[3]);
+}
+
+// The network's weights in shared memory: BF16 copies for the fragments
+// (W1, W2, W3 row-major as stored, W2 and W3 transposed for the backward
+// pass) and FP32 biases.
+struct NetW {
+    uint16_t *w1, *w2, *w3, *w2t, *w3t;
+    float *b1, *b2, *b3;
 };
 
-__device__ __forceinline__ NetSmem carve(float *base)
+constexpr int kWBytes = 2 * (NH * LW1 + NH * LW2 + NO * LW3 + NH * LW2T + NH * LW3T) + 4 * (NH + NH + NO);
+
+__device__ __forceinline__ NetW carve_w(unsigned char *base, bool transposed)
 {
-    NetSmem m;
-    m.w1t = base;
-    m.b1 = m.w1t + NI * NH;
-    m.w2t = m.b1 + NH;
-    m.b2 = m.w2t + NH * NH;
-    m.w3t = m.b2 + NH;
-    m.b3 = m.w3t + NH * NO;
-    m.x = m.b3 + NO;
-    m.h1 = m.x + kTile * NI;
-    m.h2 = m.h1 + kTile * NH;
-    m.z = m.h2 + kTile * NH;
-    m.d2 = m.z + kTile * NO;
-    m.d1 = m.d2 + kTile * NH;
+    NetW m;
+    m.w1 = reinterpret_cast<uint16_t *>(base);
+    m.w2 = m.w1 + NH * LW1;
+    m.w3 = m.w2 + NH * LW2;
+    m.w2t = m.w3 + NO * LW3;
+    m.w3t = m.w2t + (transposed ? NH * LW2T : 0);
+    float *f = reinterpret_cast<float *>(m.w3t + (transposed ? NH * LW3T : 0));
+    m.b1 = f;
+    m.b2 = f + NH;
+    m.b3 = f + 2 * NH;
     return m;
 }
 
-constexpr int kNetFloats = kP + kTile * (NI + NH + NH + NO + NH + NH);
-
-__device__ void load_weights(const uint16_t *w, const NetSmem &m)
+__device__ void load_weights(const uint16_t *w, const NetW &m, bool transposed)
 {
-    for (int i = threadIdx.x; i < NH * NI; i += blockDim.x) {
-        const int j = i / NI, k = i % NI;
-        m.w1t[k * NH + j] = bf(w[oW1 + i]);
-    }
+    for (int i = threadIdx.x; i < NH * NI; i += blockDim.x)
+        m.w1[(i / NI) * LW1 + i % NI] = w[oW1 + i];
     for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) {
         const int j = i / NH, k = i % NH;
-        m.w2t[k * NH + j] = bf(w[oW2 + i]);
+        m.w2[j * LW2 + k] = w[oW2 + i];
+        if (transposed)
+            m.w2t[k * LW2T + j] = w[oW2 + i];
     }
     for (int i = threadIdx.x; i < NO * NH; i += blockDim.x) {
         const int j = i / NH, k = i % NH;
-        m.w3t[k * NO + j] = bf(w[oW3 + i]);
+        m.w3[j * LW3 + k] = w[oW3 + i];
+        if (transposed)
+            m.w3t[k * LW3T + j] = w[oW3 + i];
     }
     for (int i = threadIdx.x; i < NH; i += blockDim.x) {
         m.b1[i] = bf(w[oB1 + i]);
@@ -234,45 +360,24 @@ __device__ void load_weights(const uint16_t *w, const NetSmem &m)
         m.b3[i] = bf(w[oB3 + i]);
 }
 
-// out[s][j] = act(b[j] + sum_k in[s][k] wt[k][j]) for the tile; J outputs
-// per thread, kThreads / kTile threads per sample.
-template <int K, int N, bool kRelu>
-__device__ __forceinline__ void dense(const float *in, const float *wt, const float *b, float *out)
-{
-    constexpr int per = N * kTile / kThreads;
-    const int s = threadIdx.x / (kThreads / kTile), j0 = (threadIdx.x % (kThreads / kTile)) * per;
-    float acc[per];
-#pragma unroll
-    for (int m = 0; m < per; m++)
-        acc[m] = b[j0 + m];
-    for (int k = 0; k < K; k++) {
-        const float v = in[s * K + k];
-#pragma unroll
-        for (int m = 0; m < per; m++)
-            acc[m] = fmaf(v, wt[k * N + j0 + m], acc[m]);
-    }
-#pragma unroll
-    for (int m = 0; m < per; m++)
-        out[s * N + j0 + m] = kRelu ? fmaxf(acc[m], 0.0f) : acc[m];
-}
-
-// Tile of samples [t0, t0 + kTile) in `order` (or in index order): inputs and
-// classes (-1 for missing / invalid ones).
+// Tile of samples [t0, t0 + kTile) in `order` (or in index order): inputs
+// (FP32 copies of the BF16 values) and classes (-1 for missing or invalid
+// ones).
 __device__ __forceinline__ void load_tile(const uint16_t *x, const uint8_t *label, const uint32_t *order,
-                                          uint32_t n, uint32_t t0, const NetSmem &m, int *s_cls)
+                                          uint32_t n, uint32_t t0, float *X, int *s_cls)
 {
     for (int i = threadIdx.x; i < kTile * NI; i += blockDim.x) {
-        const uint32_t s = i / NI, f = i % NI, g = t0 + s;
+        const uint32_t s = i / NI, f = i % NI, gs = t0 + s;
         float v = 0.0f;
-        if (g < n)
-            v = bf(x[(size_t)(order ? order[g] : g) * NI + f]);
-        m.x[i] = v;
+        if (gs < n)
+            v = bf(x[(size_t)(order ? order[gs] : gs) * NI + f]);
+        X[s * LX + f] = v;
     }
     if (s_cls && threadIdx.x < kTile) {
-        const uint32_t g = t0 + threadIdx.x;
+        const uint32_t gs = t0 + threadIdx.x;
         int c = -1;
-        if (g < n) {
-            const uint32_t lab = label[order ? order[g] : g];
+        if (gs < n) {
+            const uint32_t lab = label[order ? order[gs] : gs];
             if ((lab & 31u) < (uint32_t)kNumModes)
                 c = (int)((lab >> 5) * kNumModes + (lab & 31u));
         }
@@ -280,40 +385,94 @@ __device__ __forceinline__ void load_tile(const uint16_t *x, const uint8_t *labe
     }
 }
 
-__device__ __forceinline__ void forward_tile(const NetSmem &m)
+// Gradient tile (16 x 8) at (m0, n0) of A^T B over the tile's samples,
+// A = D [s][m] (deltas, row stride ldd) and B = H [s][n] (activations or
+// inputs, row stride ldh), added to G[m][n] (row stride ldg).
+template <bool kHExact>
+__device__ __forceinline__ void grad_tile(const float *D, int ldd, const float *H, int ldh, float *G, int ldg, int m0,
+                                          int n0)
 {
-    dense<NI, NH, true>(m.x, m.w1t, m.b1, m.h1);
-    __syncthreads();
-    dense<NH, NH, true>(m.h1, m.w2t, m.b2, m.h2);
-    __syncthreads();
-    dense<NH, NO, false>(m.h2, m.w3t, m.b3, m.z);
-    __syncthreads();
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k0 = 0; k0 < kTile; k0 += 16) {
+        uint32_t ah[4], al[4], bh[2], bl[2];
+        frag_a_cols(D, ldd, m0, k0, ah, al);
+        frag_b_rows<kHExact>(H, ldh, n0, k0, bh, bl);
+        mma_bf16(c, ah, bh);
+        mma_bf16(c, al, bh);
+        if (!kHExact)
+            mma_bf16(c, ah, bl);
+    }
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    float *r0 = G + (m0 + g) * ldg + n0 + 2 * t, *r1 = r0 + 8 * ldg;
+    r0[0] += c[0];
+    r0[1] += c[1];
+    r1[0] += c[2];
+    r1[1] += c[3];
 }
+
+// Delta tile (16 x 8) at (m0, n0) of (Dn Wn) * relu'(H): Dn the next layer's
+// deltas [s][K] (row stride ldd), Wn^T as BF16 weights [N][K], H the layer's
+// activations [s][N].
+template <int K>
+__device__ __forceinline__ void delta_tile(const float *Dn, int ldd, const uint16_t *Wt, int ldw, const float *H,
+                                           int ldh, float *D, int ld, int m0, int n0)
+{
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t ah[4], al[4], bw[2];
+        frag_a_rows<false>(Dn, ldd, m0, k0, ah, al);
+        frag_b_w(Wt, ldw, n0, k0, bw);
+        mma_bf16(c, ah, bw);
+        mma_bf16(c, al, bw);
+    }
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3, n = n0 + 2 * t;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int m = m0 + g + 8 * (q >> 1), nn = n + (q & 1);
+        D[m * ld + nn] = H[m * ldh + nn] > 0.0f ? c[q] : 0.0f;
+    }
+}
+
+constexpr int kTileFloats = kTile * (LX + LH + LH + LZ + LH + LH);
 
 __global__ void __launch_bounds__(kThreads) mlp_loss_grad_kernel(const uint16_t *w, const uint16_t *x,
                                                                   const uint8_t *label, const uint32_t *order,
                                                                   uint32_t n, float *grad, float *loss)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_cls[kTile];
     __shared__ float s_loss;
-    const NetSmem m = carve(smem);
-    float *g = smem + kNetFloats;   // [kP] gradient accumulators, flat parameter order
-    load_weights(w, m);
+    const NetW m = carve_w(smem, true);
+    float *X = reinterpret_cast<float *>(smem + kWBytes);
+    float *H1 = X + kTile * LX, *H2 = H1 + kTile * LH, *Z = H2 + kTile * LH, *D2 = Z + kTile * LZ, *D1 = D2 + kTile * LH;
+    float *g = D1 + kTile * LH;   // [kP] gradient accumulators, flat parameter order
+    load_weights(w, m, true);
     for (int i = threadIdx.x; i < kP; i += blockDim.x)
         g[i] = 0.0f;
     if (threadIdx.x == 0)
         s_loss = 0.0f;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kThreads / 32, kM = kTile / 16;
     const uint32_t ntiles = (n + kTile - 1) / kTile;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        load_tile(x, label, order, n, t * kTile, m, s_cls);
+    for (uint32_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        load_tile(x, label, order, n, tt * kTile, X, s_cls);
         __syncthreads();
-        forward_tile(m);
-        // softmax cross-entropy; z becomes d loss / d z
-        for (int s = warp; s < kTile; s += kThreads / 32) {
-            float *z = m.z + s * NO;
+        // forward: 16 x 8 output tiles spread over the warps
+        for (int q = warp; q < kM * (NH / 8); q += kWarps)
+            dense_tile<NI, true, true>(X, LX, m.w1, LW1, m.b1, H1, LH, 16 * (q % kM), 8 * (q / kM));
+        __syncthreads();
+        for (int q = warp; q < kM * (NH / 8); q += kWarps)
+            dense_tile<NH, false, true>(H1, LH, m.w2, LW2, m.b2, H2, LH, 16 * (q % kM), 8 * (q / kM));
+        __syncthreads();
+        for (int q = warp; q < kM * (NO / 8); q += kWarps)
+            dense_tile<NH, false, false>(H2, LH, m.w3, LW3, m.b3, Z, LZ, 16 * (q % kM), 8 * (q / kM));
+        __syncthreads();
+        // softmax cross-entropy; Z becomes d loss / d z
+        for (int s = warp; s < kTile; s += kWarps) {
+            float *z = Z + s * LZ;
             const int y = s_cls[s];
             float zmax = -INFINITY;
             for (int j = lane; j < NO; j += 32)
@@ -334,74 +493,37 @@ __global__ void __launch_bounds__(kThreads) mlp_loss_grad_kernel(const uint16_t 
                 z[j] = y >= 0 ? expf(z[j] - zmax) / den - (j == y ? 1.0f : 0.0f) : 0.0f;
         }
         __syncthreads();
-        // layer 3: gW3[j][i] += sum_s dz[s][j] h2[s][i]; gb3; dh2 = dz W3 * relu'
-        for (int e = threadIdx.x; e < NO * NH; e += kThreads) {
-            const int j = e / NH, i = e % NH;
-            float a = 0.0f;
-            for (int s = 0; s < kTile; s++)
-                a = fmaf(m.z[s * NO + j], m.h2[s * NH + i], a);
-            g[oW3 + e] += a;
-        }
+        // layer 3: gW3 += dz^T h2 (112 x 64), gb3; d2 = (dz W3) relu'(h2)
+        for (int q = warp; q < (NO / 16) * (NH / 8); q += kWarps)
+            grad_tile<false>(Z, LZ, H2, LH, g + oW3, NH, 16 * (q % (NO / 16)), 8 * (q / (NO / 16)));
+        for (int q = warp; q < kM * (NH / 8); q += kWarps)
+            delta_tile<NO>(Z, LZ, m.w3t, LW3T, H2, LH, D2, LH, 16 * (q % kM), 8 * (q / kM));
         for (int j = threadIdx.x; j < NO; j += kThreads) {
             float a = 0.0f;
             for (int s = 0; s < kTile; s++)
-                a += m.z[s * NO + j];
+                a += Z[s * LZ + j];
             g[oB3 + j] += a;
         }
-        {
-            const int s = threadIdx.x / 8, i0 = (threadIdx.x % 8) * 8;
-            float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int j = 0; j < NO; j++) {
-                const float dz = m.z[s * NO + j];
-#pragma unroll
-                for (int u = 0; u < 8; u++)
-                    acc[u] = fmaf(dz, m.w3t[(i0 + u) * NO + j], acc[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                m.d2[s * NH + i0 + u] = m.h2[s * NH + i0 + u] > 0.0f ? acc[u] : 0.0f;
-        }
         __syncthreads();
-        // layer 2
-        for (int e = threadIdx.x; e < NH * NH; e += kThreads) {
-            const int j = e / NH, i = e % NH;
-            float a = 0.0f;
-            for (int s = 0; s < kTile; s++)
-                a = fmaf(m.d2[s * NH + j], m.h1[s * NH + i], a);
-            g[oW2 + e] += a;
-        }
+        // layer 2: gW2 += d2^T h1 (64 x 64), gb2; d1 = (d2 W2) relu'(h1)
+        for (int q = warp; q < (NH / 16) * (NH / 8); q += kWarps)
+            grad_tile<false>(D2, LH, H1, LH, g + oW2, NH, 16 * (q % (NH / 16)), 8 * (q / (NH / 16)));
+        for (int q = warp; q < kM * (NH / 8); q += kWarps)
+            delta_tile<NH>(D2, LH, m.w2t, LW2T, H1, LH, D1, LH, 16 * (q % kM), 8 * (q / kM));
         for (int j = threadIdx.x; j < NH; j += kThreads) {
             float a = 0.0f;
             for (int s = 0; s < kTile; s++)
-                a += m.d2[s * NH + j];
+                a += D2[s * LH + j];
             g[oB2 + j] += a;
         }
-        {
-            const int s = threadIdx.x / 8, i0 = (threadIdx.x % 8) * 8;
-            float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int j = 0; j < NH; j++) {
-                const float d = m.d2[s * NH + j];
-#pragma unroll
-                for (int u = 0; u < 8; u++)
-                    acc[u] = fmaf(d, m.w2t[(i0 + u) * NH + j], acc[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                m.d1[s * NH + i0 + u] = m.h1[s * NH + i0 + u] > 0.0f ? acc[u] : 0.0f;
-        }
         __syncthreads();
-        // layer 1
-        for (int e = threadIdx.x; e < NH * NI; e += kThreads) {
-            const int j = e / NI, i = e % NI;
-            float a = 0.0f;
-            for (int s = 0; s < kTile; s++)
-                a = fmaf(m.d1[s * NH + j], m.x[s * NI + i], a);
-            g[oW1 + e] += a;
-        }
+        // layer 1: gW1 += d1^T x (64 x 48), gb1
+        for (int q = warp; q < (NH / 16) * (NI / 8); q += kWarps)
+            grad_tile<true>(D1, LH, X, LX, g + oW1, NI, 16 * (q % (NH / 16)), 8 * (q / (NH / 16)));
         for (int j = threadIdx.x; j < NH; j += kThreads) {
             float a = 0.0f;
             for (int s = 0; s < kTile; s++)
-                a += m.d1[s * NH + j];
+                a += D1[s * LH + j];
             g[oB1 + j] += a;
         }
         __syncthreads();
@@ -412,118 +534,64 @@ __global__ void __launch_bounds__(kThreads) mlp_loss_grad_kernel(const uint16_t 
         atomicAdd(loss, s_loss);
 }
 
-// Inference, register blocked: each warp takes 4 samples at a time and lane l
-// the outputs l, l + 32, ...; per input feature, one 16-byte broadcast of the
-// 4 samples' activations and one weight per output feed 4 FMAs.  The
-// activations of a warp's samples are its own columns of [feature][sample]
-// arrays (row stride kRowT keeps the 16-byte stores on distinct banks), so the
-// warps never wait on one another after the weights are loaded.
-constexpr int kRowT = kTile + 4;
-
-template <int K, int N, bool kRelu>
-__device__ __forceinline__ void dense_cols(const float *inT, const float *wt, const float *b, int lane, int col,
-                                           float acc[4][(N + 31) / 32])
-{
-    constexpr int kO = (N + 31) / 32;
-#pragma unroll
-    for (int i = 0; i < kO; i++) {
-        const int o = lane + 32 * i;
-        const float bias = o < N ? b[o] : 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            acc[q][i] = bias;
-    }
-#pragma unroll 4
-    for (int k = 0; k < K; k++) {
-        const float4 v = *reinterpret_cast<const float4 *>(inT + k * kRowT + col);
-#pragma unroll
-        for (int i = 0; i < kO; i++) {
-            const int o = lane + 32 * i;
-            const float w = o < N ? wt[k * N + o] : 0.0f;
-            acc[0][i] = fmaf(v.x, w, acc[0][i]);
-            acc[1][i] = fmaf(v.y, w, acc[1][i]);
-            acc[2][i] = fmaf(v.z, w, acc[2][i]);
-            acc[3][i] = fmaf(v.w, w, acc[3][i]);
-        }
-    }
-    if (kRelu) {
-#pragma unroll
-        for (int i = 0; i < kO; i++)
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                acc[q][i] = fmaxf(acc[q][i], 0.0f);
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void store_cols(float *outT, int lane, int col, const float acc[4][(N + 31) / 32])
-{
-#pragma unroll
-    for (int i = 0; i < (N + 31) / 32; i++) {
-        const int o = lane + 32 * i;
-        if (o < N)
-            *reinterpret_cast<float4 *>(outT + o * kRowT + col) = make_float4(acc[0][i], acc[1][i], acc[2][i], acc[3][i]);
-    }
-}
+// Inference: each warp takes 16 samples at a time through the three layers
+// on its own activation tiles (no barrier after the weights are loaded),
+// then takes the first maximum of each sample's logits.
+constexpr int kPredWarpFloats = 16 * (LX + LH + LH + LZ);
 
 __global__ void __launch_bounds__(kThreads) mlp_predict_kernel(const uint16_t *w, const uint16_t *x, uint32_t n,
                                                                 const uint32_t *index, uint8_t *label)
 {
-    extern __shared__ __align__(16) float smem[];
-    const NetSmem m = carve(smem);
-    float *xT = smem + kP, *h1T = xT + NI * kRowT, *h2T = h1T + NH * kRowT;
-    load_weights(w, m);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const NetW m = carve_w(smem, false);
+    load_weights(w, m, false);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, col = 4 * warp;
-    const uint32_t ngroups = (n + 3) / 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *X = reinterpret_cast<float *>(smem + kWBytes) + warp * kPredWarpFloats;
+    float *H1 = X + 16 * LX, *H2 = H1 + 16 * LH, *Z = H2 + 16 * LH;
+    const uint32_t ngroups = (n + 15) / 16;
     for (uint32_t grp = blockIdx.x * (kThreads / 32) + warp; grp < ngroups; grp += gridDim.x * (kThreads / 32)) {
-        const uint32_t s0 = 4 * grp;
-        for (int i = lane; i < 4 * NI; i += 32) {
+        const uint32_t s0 = 16 * grp;
+        for (int i = lane; i < 16 * NI; i += 32) {
             const int q = i / NI, f = i - q * NI;
-            xT[f * kRowT + col + q] = s0 + q < n ? bf(x[(size_t)(s0 + q) * NI + f]) : 0.0f;
+            X[q * LX + f] = s0 + q < n ? bf(x[(size_t)(s0 + q) * NI + f]) : 0.0f;
         }
         __syncwarp();
+#pragma unroll 1
+        for (int nt = 0; nt < NH / 8; nt++)
+            dense_tile<NI, true, true>(X, LX, m.w1, LW1, m.b1, H1, LH, 0, 8 * nt);
+        __syncwarp();
+#pragma unroll 1
+        for (int nt = 0; nt < NH / 8; nt++)
+            dense_tile<NH, false, true>(H1, LH, m.w2, LW2, m.b2, H2, LH, 0, 8 * nt);
+        __syncwarp();
+#pragma unroll 1
+        for (int nt = 0; nt < NO / 8; nt++)
+            dense_tile<NH, false, false>(H2, LH, m.w3, LW3, m.b3, Z, LZ, 0, 8 * nt);
+        __syncwarp();
+        // first maximum of each sample's logits: lanes 2q, 2q + 1 take sample q
         {
-            float a1[4][NH / 32];
-            dense_cols<NI, NH, true>(xT, m.w1t, m.b1, lane, col, a1);
-            store_cols<NH>(h1T, lane, col, a1);
-        }
-        __syncwarp();
-        {
-            float a2[4][NH / 32];
-            dense_cols<NH, NH, true>(h1T, m.w2t, m.b2, lane, col, a2);
-            store_cols<NH>(h2T, lane, col, a2);
-        }
-        __syncwarp();
-        float z[4][(NO + 31) / 32];
-        dense_cols<NH, NO, false>(h2T, m.w3t, m.b3, lane, col, z);
-        // first maximum of each sample's logits over the lanes
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
+            const int q = lane >> 1, half = lane & 1;
             float best = -INFINITY;
             int arg = 0;
-#pragma unroll
-            for (int i = 0; i < (NO + 31) / 32; i++) {
-                const int o = lane + 32 * i;
-                if (o < NO && z[q][i] > best) {
-                    best = z[q][i];
-                    arg = o;
+            for (int j = half; j < NO; j += 2) {
+                const float v = Z[q * LZ + j];
+                if (v > best) {
+                    best = v;
+                    arg = j;
                 }
             }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                const float ob = __shfl_xor_sync(kFull, best, d);
-                const int oa = __shfl_xor_sync(kFull, arg, d);
-                if (ob > best || (ob == best && oa < arg)) {
-                    best = ob;
-                    arg = oa;
-                }
+            const float ob = __shfl_xor_sync(kFull, best, 1);
+            const int oa = __shfl_xor_sync(kFull, arg, 1);
+            if (ob > best || (ob == best && oa < arg)) {
+                best = ob;
+                arg = oa;
             }
             const uint32_t gi = s0 + q;
-            if (lane == 0 && gi < n)
+            if (half == 0 && gi < n)
                 label[index ? index[gi] : gi] = (uint8_t)((arg % kNumModes) | (arg / kNumModes) << 5);
         }
-        __syncwarp();   // the next group overwrites this warp's columns
+        __syncwarp();   // the next group overwrites this warp's tiles
     }
 }
 
@@ -647,7 +715,7 @@ RLFC_API int rlfc_mlp_loss_grad(const uint16_t *d_w, const uint16_t *d_x, const 
         return RLFC_E_RANGE;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const size_t smem = sizeof(float) * (kNetFloats + kP);
+    const size_t smem = kWBytes + sizeof(float) * (kTileFloats + kP);
     cudaError_t e = cudaFuncSetAttribute(mlp_loss_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "rlfc_mlp_loss_grad");
@@ -686,7 +754,7 @@ RLFC_API int rlfc_mlp_predict(const uint16_t *d_w, const uint16_t *d_x, size_t n
         return RLFC_E_RANGE;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const size_t smem = sizeof(float) * (kP + (NI + 2 * NH) * kRowT);
+    const size_t smem = kWBytes + sizeof(float) * kPredWarpFloats * (kThreads / 32);
     cudaError_t e = cudaFuncSetAttribute(mlp_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "rlfc_mlp_predict");
