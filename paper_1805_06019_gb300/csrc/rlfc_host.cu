@@ -127,7 +127,8 @@ int fmt(const std::string &m)
 struct Parsed {
     uint32_t U, V, W, H, B, L, q, n_top, S;
     uint64_t off_top, off_offsets, off_records, record_words;
-    uint32_t Wp, Hp, nlx, nly, nloc, MW, max_record_words, max_strip_words, max_present;
+    uint32_t Wp, Hp, nlx, nly, nloc, MW, max_record_words, max_strip_words, max_present, max_strip_present;
+    std::vector<uint32_t> present;   // stored blocks of each record
     uint64_t max_top_mag, max_block_mag;   // largest |top value| and bound on |block value|
     Tables tab;
 };
@@ -202,6 +203,7 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
     ps.MW = (ps.S + 31) / 32;
     ps.max_record_words = 0;
     ps.max_present = 0;
+    ps.present.assign(noff - 1, 0u);
     ps.max_block_mag = 0;
     ps.max_top_mag = 0;
     for (uint64_t i = 0; i < top_bytes / 2; i++) {
@@ -230,6 +232,7 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
             P += __builtin_popcount(w);
         }
         ps.max_present = std::max(ps.max_present, P);
+        ps.present[r] = P;
         uint64_t bits = 32ull * ps.MW + 18ull * P;
         if (bits > 32ull * words)
             return fmt("block headers run past the record");
@@ -259,10 +262,15 @@ int parse(const uint8_t *p, size_t n, Parsed &ps)
     // the longest run of records of kDecodeStrip consecutive locations of a
     // row (the full decode stages one such run per CTA)
     ps.max_strip_words = 0;
+    ps.max_strip_present = 0;
     for (uint32_t y = 0; y < ps.nly; y++)
         for (uint32_t x0 = 0; x0 < ps.nlx; x0 += kDecodeStrip) {
             const uint32_t b0 = y * ps.nlx + x0, b1 = y * ps.nlx + std::min(x0 + kDecodeStrip, ps.nlx);
             ps.max_strip_words = std::max(ps.max_strip_words, rd32(off + 12ull * b1) - rd32(off + 12ull * b0));
+            uint32_t sp = 0;
+            for (uint64_t r = 3ull * b0; r < 3ull * b1; r++)
+                sp += ps.present[r];
+            ps.max_strip_present = std::max(ps.max_strip_present, sp);
         }
     if (ps.B != 4) {
         set_error("the GPU kernels decode 4x4 blocks only");
@@ -303,6 +311,7 @@ int load(const uint8_t *bytes, size_t nbytes, cudaStream_t st, rlfc_stream **out
     s->max_record_words = ps.max_record_words;
     s->max_strip_words = ps.max_strip_words;
     s->max_present = ps.max_present;
+    s->max_strip_present = ps.max_strip_present;
     rlfc_info &in = s->info;
     in.U = ps.U; in.V = ps.V; in.W = ps.W; in.H = ps.H; in.B = ps.B; in.L = ps.L; in.q = ps.q;
     in.n_top = ps.n_top; in.S = ps.S; in.Wp = ps.Wp; in.Hp = ps.Hp;

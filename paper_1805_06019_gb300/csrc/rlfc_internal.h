@@ -40,6 +40,7 @@ struct rlfc_stream {
     uint32_t max_record_words = 0;
     uint32_t max_strip_words = 0;    // records of kDecodeStrip consecutive locations of a row
     uint32_t max_present = 0;        // most stored blocks in one record
+    uint32_t max_strip_present = 0;  // most stored blocks in the records of kDecodeStrip consecutive locations of a row
     // device buffers
     uint32_t *d_records = nullptr;   // record_words + kPadWords
     uint32_t *d_offsets = nullptr;   // 3 * nloc + 1
