@@ -83,6 +83,25 @@ def test_decode_all_matches_oracle(rlfc, name):
         assert np.array_equal(got, lf)
 
 
+@pytest.mark.parametrize("name", ["tiny_preset", "lossless", "wide_strip", "odd_sizes_3lvl"])
+@pytest.mark.parametrize("offset", [1, 4, 8])
+def test_decode_all_unaligned_output(rlfc, name, offset):
+    """An output that starts 1, 4 or 8 bytes past an aligned address takes
+    the 4-byte or 1-byte write paths instead of whole 16-byte chunks: the
+    same bytes, and nothing written around the output."""
+    _, data, _ = _case(name)
+    ref = oracle.Stream(data).decode_all()
+    st = rlfc.Stream(data)
+    n = ref.size
+    buf = torch.full((n + 32,), 0xA5, dtype=torch.uint8, device="cuda")
+    st.decode_all(buf[offset:offset + n].view(ref.shape))
+    torch.cuda.synchronize()
+    b = buf.cpu().numpy()
+    assert np.array_equal(b[offset:offset + n].reshape(ref.shape), ref), _mismatch(
+        b[offset:offset + n].reshape(ref.shape), ref)
+    assert (b[:offset] == 0xA5).all() and (b[offset + n:] == 0xA5).all()
+
+
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
 def test_decode_blocks_matches_oracle(rlfc, name):
     _, data, _ = _case(name)
