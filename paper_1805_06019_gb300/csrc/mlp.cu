@@ -2,11 +2,12 @@
 // statistics, and a 48 -> 64 -> 64 -> 112 perceptron with its training
 // (forward, softmax cross-entropy, backward, Adam) and inference kernels.
 //
-// Numerics: parameters and inputs are stored in BF16; every product, sum and
-// activation is FP32 (BF16 values widen exactly).  The network is small
-// (14 576 parameters, layers 48 to 112 wide), so the kernels keep the
-// transposed weights, the gradient accumulators and one tile of 32 samples'
-// activations in shared memory and use the FP32 SIMT pipes.
+// Numerics: parameters and inputs are stored in BF16; sums and activations
+// are FP32.  The network is small (14 576 parameters, layers 48 to 112 wide),
+// so the kernels keep the transposed weights, the gradient accumulators and
+// one tile of 32 samples' activations in shared memory; the products run on
+// the tensor pipe (BF16 MMA with FP32 accumulation, FP32 operands split into
+// two BF16 terms; see the tile helpers below).
 //
 // Parameter order (flat): W1 [64][48], b1 [64], W2 [64][64], b2 [64],
 // W3 [112][64], b3 [112]; rows are output units.  Class c = s * 28 + k.
