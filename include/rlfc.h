@@ -518,6 +518,30 @@ RLFC_API int rlfc_mlp_adam(float *d_master, uint16_t *d_w, float *d_grad, float 
 RLFC_API int rlfc_mlp_predict(const uint16_t *d_w, const uint16_t *d_x, size_t n, const uint32_t *d_index,
                               uint8_t *d_label, void *cuda_stream);
 
+/*
+ * Debug builds: the flags the device bounds checks raised for stream s.
+ *
+ * A library built with RLFC_DEBUG (the build script's debug option) checks,
+ * in the full decode, the per-request decode and the binned decode, every
+ * stored block before it is decoded: its mode index is one of the 28 BISE
+ * modes, its 18-bit header lies in its record's header area, and its payload
+ * lies inside its record (Algorithm 2's record layout, Section 3.4); the
+ * full decode also checks every output view index.  A failed check sets a
+ * bit in a flag word the stream owns and the block is treated as absent (the
+ * output view is skipped): nothing is read or written out of range and no
+ * kernel traps.  Bits: 1 mode, 2 header, 4 payload, 8 output index.  The
+ * loader validates every record, so a stream it accepted raises no flag;
+ * the checks guard the decoders' own index arithmetic, in place of a memory
+ * checker.
+ *
+ * Writes the flags to *flags (host memory) after the device has finished
+ * the work queued so far (the call synchronises the device), and clears them
+ * when reset is nonzero.  The paper has no counterpart.  Errors:
+ * RLFC_E_INVALID_ARG (null s or flags), RLFC_E_UNSUPPORTED (a release build,
+ * *flags = 0), RLFC_E_CUDA.
+ */
+RLFC_API int rlfc_debug_flags(const rlfc_stream *s, uint32_t *flags, int reset);
+
 /* Free a host buffer returned by the library. */
 RLFC_API void rlfc_free_host(void *p);
 

@@ -122,6 +122,8 @@ struct Args {
     uint32_t node_smem;      // the node table is cached in shared memory
     uint32_t stage_words;    // shared-memory words for the strip's records (0: read them from the stream)
     uint32_t lvl_begin[kMaxLevels];  // first BFS position of each internal level, top level first; [L-2] = n_int
+    uint32_t *dbg;           // debug builds: the stream's flag word
+    uint32_t n_out;          // output views (or slots of the packed instantiation)
 };
 
 template <bool kPacked>
@@ -336,6 +338,9 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
     __shared__ uint32_t s_roff[kRecs];
     __shared__ uint32_t s_np[kRecs];      // stored blocks of each record of the strip
     __shared__ uint32_t s_obase[kRecs];   // where each record's payload offsets start in m_off
+#ifdef RLFC_DEBUG
+    __shared__ uint32_t s_rbits[kRecs];   // length of each record in bits
+#endif
     __shared__ uint32_t s_unit;   // next unit of view work
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bx0 = blockIdx.x * kNL, by = blockIdx.y;
@@ -369,6 +374,10 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
     const uint32_t *rb = staged ? m.stage : a.records;   // records base: smem copy or stream
     if (tid < kRecs)
         s_roff[tid] = tid < 3 * (int)nl ? __ldg(a.offsets + 3 * b0 + tid) - (staged ? w_lo : 0u) : 0u;
+#ifdef RLFC_DEBUG
+    if (tid < kRecs)
+        s_rbits[tid] = tid < 3 * (int)nl ? 32u * (__ldg(a.offsets + 3 * b0 + tid + 1) - __ldg(a.offsets + 3 * b0 + tid)) : 0u;
+#endif
     {
         const uint32_t *tg = reinterpret_cast<const uint32_t *>(a.top);
         for (uint32_t i = tid; i < a.n_top * kNL * 24; i += kThreads) {
@@ -470,8 +479,18 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
                     const uint32_t *rec = rb + s_roff[r];
                     const uint32_t bp = hdr0 + kHdrBits * rank;
                     const uint32_t hdr = __funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 0x3FFFFu;
-                    decode_block_pairs(rec, m_off[(c == 0 ? ob0 : c == 1 ? ob1 : ob2) + rank], hdr, a.q, s_mode,
-                                       s_dig, v);
+                    const uint32_t pos = m_off[(c == 0 ? ob0 : c == 1 ? ob1 : ob2) + rank];
+#ifdef RLFC_DEBUG
+                    if (RLFC_DBG_BLOCK_OK(a.dbg, hdr & 31u, bp + kHdrBits, hdr0 + kHdrBits * s_np[r], pos,
+                                          (hdr & 31u) < (uint32_t)kNumModes ? mode_bits(s_mode[hdr & 31u]) : 0u,
+                                          s_rbits[r]))
+                        decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, v);
+                    else
+                        for (int j = 0; j < 8; j++)
+                            v[j] = kB2;
+#else
+                    decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, v);
+#endif
                 } else {
 #pragma unroll
                     for (int j = 0; j < 8; j++)
@@ -535,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
             const uint32_t info = nodes[w * 32 + ub + lane];
             par_v = (node_parent(info) - a.par_base) * 4 * CH;
             const uint32_t ov = a.slot_of ? __ldg(a.slot_of + node_view(info)) : node_view(info);
-            out_v = out_px<kPacked>(a, ov, by * 4, bx0 * 4);
+            out_v = RLFC_DBG_INDEX_OK(a.dbg, ov, a.n_out) ? out_px<kPacked>(a, ov, by * 4, bx0 * 4) : nullptr;
         }
         // (a) the buffer starts as every view's parent rows (RGB), the exact
         // result for every block without a stored residual; lane = (row,
@@ -606,7 +625,18 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
                 const uint32_t bp = hdr0 + kHdrBits * rank;
                 const uint32_t hdr = __funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 0x3FFFFu;
                 uint32_t dv[8];
+#ifdef RLFC_DEBUG
+                const uint32_t pos = m_off[s_obase[r] + rank];
+                if (RLFC_DBG_BLOCK_OK(a.dbg, hdr & 31u, bp + kHdrBits, hdr0 + kHdrBits * s_np[r], pos,
+                                      (hdr & 31u) < (uint32_t)kNumModes ? mode_bits(s_mode[hdr & 31u]) : 0u,
+                                      s_rbits[r]))
+                    decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, dv);
+                else
+                    for (int j = 0; j < 8; j++)
+                        dv[j] = kB2;
+#else
                 decode_block_pairs(rec, m_off[s_obase[r] + rank], hdr, a.q, s_mode, s_dig, dv);
+#endif
                 uint4 *d = reinterpret_cast<uint4 *>(wslots + t * 8);
                 d[0] = make_uint4(dv[0], dv[1], dv[2], dv[3]);
                 d[1] = make_uint4(dv[4], dv[5], dv[6], dv[7]);
@@ -646,7 +676,7 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
             for (uint32_t vv = 0; vv < (uint32_t)kUnit; vv++) {
                 uint8_t *o = reinterpret_cast<uint8_t *>(
                     __shfl_sync(kFullMask, reinterpret_cast<unsigned long long>(out_v), vv));
-                if (((sel >> (ub + vv)) & 1u) && f_act && f_rr < nrows)
+                if (((sel >> (ub + vv)) & 1u) && f_act && f_rr < nrows && o)
                     reinterpret_cast<uint4 *>(o + f_rr * row_bytes)[f_c] = wbuf[vv * 4 * CH + lane];
             }
         } else {
@@ -656,9 +686,9 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
             const uint32_t unit = (a.vec4 && piece % 4 == 0) ? 4u : 1u, per = piece / unit;
             for (uint32_t i = lane; i < kUnit * 4 * per; i += 32) {
                 const uint32_t vv = i / (4 * per), rr = (i / per) & 3u, k = i % per;
-                if (((sel >> (ub + vv)) & 1u) && rr < nrows) {
-                    const uint32_t view = node_view(nodes[w * 32 + ub + vv]);
-                    const uint32_t ov = a.slot_of ? __ldg(a.slot_of + view) : view;
+                const uint32_t view = ((sel >> (ub + vv)) & 1u) ? node_view(nodes[w * 32 + ub + vv]) : 0u;
+                const uint32_t ov = ((sel >> (ub + vv)) & 1u) ? (a.slot_of ? __ldg(a.slot_of + view) : view) : 0u;
+                if (((sel >> (ub + vv)) & 1u) && rr < nrows && RLFC_DBG_INDEX_OK(a.dbg, ov, a.n_out)) {
                     uint8_t *dst = out_px<kPacked>(a, ov, by * 4 + rr, bx0 * 4) + k * unit;
                     const uint8_t *src = bb + (vv * 4 + rr) * (kNL * 4 * BPP) + k * unit;
                     if (unit == 4)
@@ -673,7 +703,8 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
 }
 
 template <bool kPacked>
-int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, const uint32_t *slot_of, cudaStream_t st)
+int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, const uint32_t *slot_of, uint32_t n_out,
+                  cudaStream_t st)
 {
     const Tables &t = s->tab;
     Args a;
@@ -719,6 +750,8 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.pmax = std::max<uint32_t>(s->max_strip_present, 1);
     a.n_units = (t.S + kUnit - 1) / kUnit;
     a.node_smem = t.S <= kNodeSmemMax;
+    a.dbg = s->d_debug;
+    a.n_out = n_out;
     // internal levels in BFS order: L-2 first, down to 1
     for (uint32_t k = 0; k < (uint32_t)kMaxLevels; k++)
         a.lvl_begin[k] = t.n_int;
@@ -761,13 +794,13 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
 
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st)
 {
-    return launch_decode<false>(s, d_out, nullptr, nullptr, st);
+    return launch_decode<false>(s, d_out, nullptr, nullptr, s->tab.n_views, st);
 }
 
 int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, const uint32_t *slot_of,
-                         cudaStream_t st)
+                         uint32_t n_slots, cudaStream_t st)
 {
-    return launch_decode<true>(s, reinterpret_cast<uint8_t *>(d_out), needed, slot_of, st);
+    return launch_decode<true>(s, reinterpret_cast<uint8_t *>(d_out), needed, slot_of, n_slots, st);
 }
 
 }  // namespace rlfc

@@ -186,6 +186,7 @@ struct DecArgs {
     uint32_t *queue;
     uint32_t nloc, L, q, MW, level, pmax, locs_per_pop, stage, stage_words, warp_words, aligned;
     uint32_t anc_words;       // view_anc words cached in shared memory (0: read it from global)
+    uint32_t *dbg;            // debug builds: the stream's flag word
 };
 
 // Per-warp shared-memory words for a configuration (the CTA adds the cached
@@ -325,6 +326,17 @@ __global__ void __launch_bounds__(512) decode_binned_kernel(const DecArgs a)
                     const uint32_t rank = code & 0xFFFFu, c = (code >> 16) & 3u, slot = code >> 18;
                     const uint32_t *rc = base + (c == 0 ? 0u : (c == 1 ? d1 : d2));
                     const BlockHeader h = unpack_header(get_bits(rc, hdr0 + kHdrBits * rank, kHdrBits));
+#ifdef RLFC_DEBUG
+                    {
+                        const uint32_t rec_words = c == 0 ? d1 : (c == 1 ? d2 - d1 : span - d2);
+                        const uint32_t P = s_mpre[c * a.MW + a.MW - 1] + __popc(s_mask[c * a.MW + a.MW - 1]);
+                        if (!RLFC_DBG_BLOCK_OK(a.dbg, h.mode, hdr0 + kHdrBits * (rank + 1), hdr0 + kHdrBits * P,
+                                               s_off[c * a.pmax + rank],
+                                               h.mode < (uint32_t)kNumModes ? mode_bits(s_modes[h.mode]) : 0u,
+                                               32u * rec_words))
+                            continue;
+                    }
+#endif
                     int32_t u[kVals];
                     bise_decode16(rc, s_off[c * a.pmax + rank], s_modes[h.mode], u);
                     const int32_t scale = 1 << (a.q + h.shift);
@@ -488,6 +500,7 @@ int enqueue(rlfc_batch *b, const rlfc_batch_config &cfg, const uint32_t *view, c
     { TraceScope trace_("bin_scatter_kernel", st); bin_scatter_kernel<<<g, 256, 0, st>>>(ba); }
 
     DecArgs da;
+    da.dbg = s->d_debug;
     da.records = s->d_records;
     da.offsets = s->d_offsets;
     da.top = s->d_top;

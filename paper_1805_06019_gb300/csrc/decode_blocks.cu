@@ -138,6 +138,7 @@ int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uin
     a.sv.L = s->tab.L;
     a.sv.q = s->info.q;
     a.sv.MW = s->MW;
+    a.sv.dbg = s->d_debug;
     a.req_view = d_view;
     a.req_loc = d_loc;
     a.out = d_out;

@@ -278,6 +278,7 @@ int launch_render(const rlfc_stream *s, const float *d_uv, const float *d_disp, 
     a.sv.L = s->tab.L;
     a.sv.q = s->info.q;
     a.sv.MW = s->MW;
+    a.sv.dbg = s->d_debug;
     a.uv = d_uv;
     a.disp = d_disp;
     a.out = d_out;

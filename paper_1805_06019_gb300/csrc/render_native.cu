@@ -787,6 +787,7 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
     a.sv.L = s->tab.L;
     a.sv.q = s->info.q;
     a.sv.MW = s->MW;
+    a.sv.dbg = s->d_debug;
     a.uv = d_uv;
     a.disp = d_disp;
     a.out = d_out;
@@ -869,7 +870,7 @@ int launch_render_native(const rlfc_stream *s, const float *d_uv, const float *d
         if (rc == RLFC_OK) {
             { rlfc::TraceScope trace_("mark_needed_kernel", st); mark_needed_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, needed); }
             { rlfc::TraceScope trace_("assign_slots_kernel", st); assign_slots_kernel<<<1, kListThreads, 0, st>>>(needed, a.sv.n_views, slot_of); }
-            rc = launch_decode_packed(s, decoded, needed, slot_of, st);
+            rc = launch_decode_packed(s, decoded, needed, slot_of, (uint32_t)n_slots, st);
         }
         a.decoded = decoded;
         a.slot_of = slot_of;

@@ -34,6 +34,50 @@ __device__ __forceinline__ uint32_t mode_bits(uint32_t m) { return m & 0xFFu; }
 __device__ __forceinline__ uint32_t mode_b(uint32_t m) { return (m >> 8) & 0xFu; }
 __device__ __forceinline__ uint32_t mode_kind(uint32_t m) { return m >> 12; }
 
+// Bounds checks of debug builds (compiled with RLFC_DEBUG).  Before a stored
+// block is decoded, the decoders check it against its record: the mode index
+// is one of the 28, the 18-bit header lies in the record's header area, and
+// the payload lies inside the record.  A failed check sets its bit in the
+// stream's flag word (rlfc_debug_flags) and the block is treated as absent,
+// so nothing is read outside the record and the kernel never traps.  Release
+// builds compile the checks away (the macro is `true`).
+constexpr uint32_t kDbgMode = 1u;      // mode index >= 28
+constexpr uint32_t kDbgHeader = 2u;    // header past the record's header area
+constexpr uint32_t kDbgPayload = 4u;   // payload past the end of the record
+constexpr uint32_t kDbgOutput = 8u;    // an output index out of range
+#ifdef RLFC_DEBUG
+// hdr_end: the bit after the block's header; hdr_area: the bit after the
+// record's last header; pos, pay_bits: the payload; rec_bits: the record's
+// length in bits.  `pay_bits` is read only for a valid mode.
+__device__ __forceinline__ bool dbg_block_ok(uint32_t *flags, uint32_t mode, uint32_t hdr_end, uint32_t hdr_area,
+                                             uint32_t pos, uint32_t pay_bits, uint32_t rec_bits)
+{
+    uint32_t bad = 0;
+    if (mode >= (uint32_t)kNumModes)
+        bad |= kDbgMode;
+    if (hdr_end > hdr_area || hdr_area > rec_bits)
+        bad |= kDbgHeader;
+    if (mode < (uint32_t)kNumModes && (uint64_t)pos + pay_bits > rec_bits)
+        bad |= kDbgPayload;
+    if (bad && flags)
+        atomicOr(flags, bad);
+    return bad == 0;
+}
+__device__ __forceinline__ bool dbg_index_ok(uint32_t *flags, uint64_t i, uint64_t n)
+{
+    if (i < n)
+        return true;
+    if (flags)
+        atomicOr(flags, kDbgOutput);
+    return false;
+}
+#define RLFC_DBG_BLOCK_OK(...) ::rlfc::dbg_block_ok(__VA_ARGS__)
+#define RLFC_DBG_INDEX_OK(...) ::rlfc::dbg_index_ok(__VA_ARGS__)
+#else
+#define RLFC_DBG_BLOCK_OK(...) true
+#define RLFC_DBG_INDEX_OK(...) true
+#endif
+
 // Bits [pos, pos + width) of a little-endian word array, width <= 32.  Reads
 // words pos/32 and pos/32 + 1, so buffers carry one word of padding.
 __device__ __forceinline__ uint32_t get_bits(const uint32_t *w, uint32_t pos, uint32_t width)

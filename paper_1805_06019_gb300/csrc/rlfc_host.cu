@@ -290,6 +290,8 @@ void free_device(rlfc_stream *s)
     cudaFree(s->d_top);
     cudaFree(s->d_node_info);
     cudaFree(s->d_view_anc);
+    cudaFree(s->d_debug);
+    s->d_debug = nullptr;
     s->d_records = nullptr;
     s->d_offsets = nullptr;
     s->d_top = nullptr;
@@ -345,7 +347,11 @@ int load(const uint8_t *bytes, size_t nbytes, cudaStream_t st, rlfc_stream **out
         (e = cudaMalloc(&s->d_offsets, off_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_top, top_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_node_info, ni_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_view_anc, va_bytes)) != cudaSuccess) {
+        (e = cudaMalloc(&s->d_view_anc, va_bytes)) != cudaSuccess
+#ifdef RLFC_DEBUG
+        || (e = cudaMalloc(&s->d_debug, 4)) != cudaSuccess || (e = cudaMemsetAsync(s->d_debug, 0, 4, st)) != cudaSuccess
+#endif
+    ) {
         free_device(s);
         delete s;
         return cuda_fail(e, "device allocation for the stream");
@@ -426,6 +432,28 @@ void rlfc_free_stream(rlfc_stream *s)
     cudaDeviceSynchronize();
     free_device(s);
     delete s;
+}
+
+int rlfc_debug_flags(const rlfc_stream *s, uint32_t *flags, int reset)
+{
+    if (!s || !flags) {
+        set_error("null argument");
+        return RLFC_E_INVALID_ARG;
+    }
+    *flags = 0;
+    if (!s->d_debug) {
+        set_error("the library was built without RLFC_DEBUG");
+        return RLFC_E_UNSUPPORTED;
+    }
+    DeviceGuard g(s->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(flags, s->d_debug, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset)
+        e = cudaMemset(s->d_debug, 0, 4);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the debug flags");
+    return RLFC_OK;
 }
 
 int rlfc_decode_all(const rlfc_stream *s, uint8_t *d_out, void *cuda_stream)

@@ -47,6 +47,7 @@ struct rlfc_stream {
     int16_t *d_top = nullptr;        // [n_top][nloc][3][16], block-major YCoCg-R
     uint32_t *d_node_info = nullptr; // [S]
     uint32_t *d_view_anc = nullptr;  // [n_views][kMaxLevels]
+    uint32_t *d_debug = nullptr;     // debug builds: the bounds checks' flag word (rlfc_debug_flags)
 };
 
 namespace rlfc {
@@ -92,9 +93,10 @@ int cuda_fail(cudaError_t e, const char *what);
 int launch_decode_all(const rlfc_stream *s, uint8_t *d_out, cudaStream_t st);
 // every view the mask marks (all when null), as packed RGB words [view][H][W]
 // Packed RGB words of the views `needed` marks, view v into slot slot_of[v]
-// of d_out ([slot][H][W]); with needed null, every view v into slot v.
+// of d_out ([slot][H][W], n_slots slots); with needed null, every view v into
+// slot v.
 int launch_decode_packed(const rlfc_stream *s, uint32_t *d_out, const uint8_t *needed, const uint32_t *slot_of,
-                         cudaStream_t st);
+                         uint32_t n_slots, cudaStream_t st);
 // Largest |value| of any stored block of the stream, decoded (synchronous).
 int block_magnitude(const rlfc_stream *s, cudaStream_t st, uint32_t *mag);
 int launch_decode_blocks(const rlfc_stream *s, const uint32_t *d_view, const uint32_t *d_loc,

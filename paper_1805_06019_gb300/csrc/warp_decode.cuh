@@ -23,6 +23,7 @@ struct StreamView {
     const int16_t *top;
     const uint32_t *view_anc;
     uint32_t n_views, nloc, nlx, L, q, MW;
+    uint32_t *dbg = nullptr;   // debug builds: the stream's flag word (rlfc_debug_flags)
 };
 
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x, int lane)
@@ -123,8 +124,18 @@ __device__ __forceinline__ uint32_t warp_decode_block(const StreamView &sv, cons
             int32_t val = 0;
             if (in_tree && present) {
                 const BlockHeader h = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
-                const uint32_t u = bise_value(rec, off, s_mode[h.mode], v);
-                val = (h.min + (int32_t)u) * (1 << (sv.q + h.shift));
+#ifdef RLFC_DEBUG
+                const uint32_t rec_bits = 32u * (sv.offsets[3 * loc + c + 1] - sv.offsets[3 * loc + c]);
+                const bool ok = RLFC_DBG_BLOCK_OK(sv.dbg, h.mode, hdr0 + kHdrBits * (rank + 1), pay0, off,
+                                                  h.mode < (uint32_t)kNumModes ? mode_bits(s_mode[h.mode]) : 0u,
+                                                  rec_bits);
+#else
+                constexpr bool ok = true;
+#endif
+                if (ok) {
+                    const uint32_t u = bise_value(rec, off, s_mode[h.mode], v);
+                    val = (h.min + (int32_t)u) * (1 << (sv.q + h.shift));
+                }
             }
             val += __shfl_down_sync(kFullMask, val, 16);
             acc += val;

@@ -13,7 +13,7 @@ import threading
 
 import torch
 
-from .buildlib import LIB
+from .buildlib import LIB, LIB_DEBUG
 
 RLFC_OK = 0
 RLFC_E_RANGE = 6   # a size beyond what the call supports (include/rlfc.h)
@@ -70,14 +70,17 @@ EXPORTS = ["rlfc_load_stream", "rlfc_stream_info", "rlfc_free_stream", "rlfc_dec
            "rlfc_batch_autotune", "rlfc_batch_free", "rlfc_server_create", "rlfc_server_add",
            "rlfc_server_submit", "rlfc_server_submit_u8", "rlfc_server_poll", "rlfc_server_now", "rlfc_server_free",
            "rlfc_ks_search", "rlfc_ks_compact", "rlfc_ks_features", "rlfc_mlp_loss_grad", "rlfc_mlp_adam",
-           "rlfc_mlp_predict"]
+           "rlfc_mlp_predict", "rlfc_debug_flags"]
 
 _lib = None
 _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return LIB
+    """The library this process binds: the release build, or the debug build
+    (device bounds checks, rlfc_debug_flags) when RLFC_DEBUG_LIBRARY=1 is set
+    before the first call."""
+    return LIB_DEBUG if os.environ.get("RLFC_DEBUG_LIBRARY") == "1" else LIB
 
 
 def lib():
@@ -85,9 +88,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB):
-                raise RuntimeError(f"librlfc.so not built ({LIB}); run paper_1805_06019_gb300.build()")
-            L = ctypes.CDLL(LIB)
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"librlfc.so not built ({path}); run paper_1805_06019_gb300.build()")
+            L = ctypes.CDLL(path)
             vp, sz, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32
             L.rlfc_load_stream.argtypes = [vp, sz, vp, ctypes.POINTER(vp)]
             L.rlfc_stream_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -133,6 +137,7 @@ def lib():
             L.rlfc_mlp_predict.argtypes = [vp, vp, sz, vp, vp, vp]
             L.rlfc_trace_enable.argtypes = [ctypes.c_int]
             L.rlfc_trace_read.argtypes = [ctypes.POINTER(TraceEntry), sz, ctypes.POINTER(sz), ctypes.c_int]
+            L.rlfc_debug_flags.argtypes = [vp, ctypes.POINTER(u32), ctypes.c_int]
             _lib = L
         return _lib
 
@@ -201,6 +206,13 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+    def debug_flags(self, reset: bool = True) -> int:
+        """The flags the device bounds checks raised for this stream
+        (rlfc_debug_flags; debug builds only, raises RLFCError otherwise)."""
+        f = ctypes.c_uint32(0)
+        _check(lib().rlfc_debug_flags(self._h, ctypes.byref(f), 1 if reset else 0))
+        return int(f.value)
 
     def decode_all(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Every view: [U*V, H, W, 3] uint8 (rlfc_decode_all)."""

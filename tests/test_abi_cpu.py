@@ -45,6 +45,19 @@ def test_binding_lists_the_header(lib):
     assert sorted(rlfc.EXPORTS) == _declared()
 
 
+def test_debug_build_exports_the_same_symbols_and_refuses_null_arguments(lib):
+    """The RLFC_DEBUG build (device bounds checks) has the same C ABI; the
+    flag query refuses null arguments before any device call, in both builds."""
+    dbg = ctypes.CDLL(pkg_build.build(debug=True))
+    for n in _declared():
+        assert hasattr(dbg, n), n
+    f = ctypes.c_uint32(7)
+    for L in (lib, dbg):
+        L.rlfc_debug_flags.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        assert L.rlfc_debug_flags(None, ctypes.byref(f), 0) == E_INVALID_ARG
+        assert L.rlfc_debug_flags(None, None, 1) == E_INVALID_ARG
+
+
 def test_strerror_covers_every_code(lib):
     texts = [lib.rlfc_strerror(c).decode() for c in range(8)]
     assert len(set(texts)) == 8
