@@ -13,22 +13,27 @@
 //     reconstruction is the parent reconstruction (or top RKV) plus the
 //     decoded residual where a block is stored; then the location's rows of
 //     every parent of a view are converted to RGB once; one barrier, then
-//  3. the views, one unit of 16 BFS positions at a time per warp (each warp
-//     takes the next unit from a shared counter and never waits for the
-//     others):
-//     a. every block of the unit is written as its parent's RGB, the exact
+//  3. the views, one unit of kUnit (8) BFS positions at a time per warp
+//     (each warp takes the next unit from a shared counter and never waits
+//     for the others).  The unit's output rows (8 views x 4 block rows x
+//     the strip's 96 bytes) are assembled in the warp's shared-memory
+//     buffer and written once:
+//     a. the buffer starts as every view's parent rows (RGB), the exact
 //        result for every block without a stored residual (most of them);
-//     b. then the unit's items (a view's block with at least one stored
-//        channel) and slots (a stored channel block): lane = (view, half of
-//        the strip) reads the three channel masks of its four locations,
-//        and one warp scan of the per-lane counts places every item and
-//        slot; lanes whose slots do not fit the warp's kWSlots decode slots
-//        go in a further run.  Every slot is decoded by one lane (a
-//        mode-generic BISE decoder that builds two values per
-//        multiply-add, see decode_block_pairs); then four lanes per item,
-//        one block row each, add the residual rows to the parent rows,
-//        apply the inverse YCoCg-R two pixels per instruction and overwrite
-//        the parent copy.
+//     b. the unit's items (a view's block with at least one stored channel)
+//        and slots (a stored channel block): lane = (view, quarter of the
+//        strip) reads the three channel masks of its two locations, and one
+//        warp scan of the per-lane counts places every item and slot; lanes
+//        whose slots do not fit the warp's kWSlots decode slots go in a
+//        further run.  Every slot is decoded by one lane (a mode-generic
+//        BISE decoder that builds two values per multiply-add, see
+//        decode_block_pairs); then four lanes per item, one block row each,
+//        add the residual rows to the parent rows, apply the inverse
+//        YCoCg-R two pixels per instruction and overwrite the item's bytes
+//        in the buffer;
+//     c. the buffer is written as whole 16-byte chunks, consecutive lanes
+//        on consecutive chunks of one view row (one large L2 write per view
+//        row instead of one per block row).
 // Reconstructions are 16-bit values plus a bias of 2^14, two to a word (the
 // loader refuses streams whose values could leave that range).  Every stored
 // block of the strip is decoded once.
