@@ -118,10 +118,8 @@ struct Args {
     uint32_t par_base;       // BFS position (or top index) of the first parent of a view
     uint32_t n_par;          // parents of views
     uint32_t nlx, nloc, W, H;
-    uint32_t vec16;          // 16-byte stores of 4-location groups are aligned (RGB: W % 16 == 0; packed: W % 4 == 0)
-    uint32_t vec4;           // 4-byte stores of one location's row are aligned (W % 4 == 0)
-    uint32_t vec8;           // RGB: 8-byte stores at even locations are aligned (W % 8 == 0)
-    uint32_t sec32;          // every strip row starts on a 32-byte boundary (RGB: W % 32 == 0; packed: W % 8 == 0)
+    uint32_t vec16;          // a strip's view rows go out as whole 16-byte chunks (16-byte aligned output; RGB: W % 16 == 0, packed: W % 4 == 0)
+    uint32_t vec4;           // where they cannot, as 4-byte words (4-byte aligned output; RGB also W % 4 == 0)
     uint32_t pmax;           // largest number of stored blocks in the records of one strip
     uint32_t n_units;        // ceil(S / kUnit)
     uint32_t node_smem;      // the node table is cached in shared memory
@@ -293,38 +291,6 @@ __device__ __forceinline__ void row_to_rgb(const uint2 y, const uint2 co, const 
         w[1] = __byte_perm(__byte_perm(t01, b01, 0x0063), t23, 0x5410);
         w[2] = __byte_perm(b23, t23, 0x2760);
         w[3] = 0;
-    }
-}
-
-// Store one location's block row (four pixels from column x) at dst, the
-// output address of pixel x of that row.
-template <bool kPacked>
-__device__ __forceinline__ void store_row(const Args &a, uint8_t *dst, uint32_t x, const uint32_t w[4])
-{
-    const bool whole = x + 4 <= a.W;
-    if (kPacked) {
-        uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-        if (whole && a.vec16) {
-            *reinterpret_cast<uint4 *>(d) = make_uint4(w[0], w[1], w[2], w[3]);
-        } else {
-            for (uint32_t k = 0; k < 4 && x + k < a.W; k++)
-                d[k] = w[k];
-        }
-    } else {
-        if (whole && a.vec8) {
-            // 12 bytes in two stores: 8 + 4 at an even location, 4 + 8 at an odd one
-            const bool even = ((x >> 2) & 1u) == 0;
-            *reinterpret_cast<uint2 *>(dst + (even ? 0 : 4)) = even ? make_uint2(w[0], w[1]) : make_uint2(w[1], w[2]);
-            *reinterpret_cast<uint32_t *>(dst + (even ? 8 : 0)) = even ? w[2] : w[0];
-        } else if (whole && a.vec4) {
-            uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-            d[0] = w[0];
-            d[1] = w[1];
-            d[2] = w[2];
-        } else {
-            for (uint32_t k = 0; k < 12 && x + k / 3 < a.W; k++)
-                dst[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
-        }
     }
 }
 
@@ -743,14 +709,10 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     }
     if (kPacked) {
         a.vec16 = ((uintptr_t)d_out & 15u) == 0 && (a.W & 3u) == 0;
-        a.vec4 = a.vec16;
-        a.vec8 = 0;
-        a.sec32 = ((uintptr_t)d_out & 31u) == 0 && (a.W & 7u) == 0;
+        a.vec4 = ((uintptr_t)d_out & 3u) == 0;
     } else {
         a.vec16 = ((uintptr_t)d_out & 15u) == 0 && (a.W & 15u) == 0;
         a.vec4 = ((uintptr_t)d_out & 3u) == 0 && (a.W & 3u) == 0;
-        a.vec8 = ((uintptr_t)d_out & 7u) == 0 && (a.W & 7u) == 0;
-        a.sec32 = ((uintptr_t)d_out & 31u) == 0 && (a.W & 31u) == 0;
     }
     a.pmax = std::max<uint32_t>(s->max_strip_present, 1);
     a.n_units = (t.S + kUnit - 1) / kUnit;
