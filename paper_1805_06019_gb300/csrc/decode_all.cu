@@ -64,7 +64,7 @@ constexpr size_t kCtaSmemTarget = 111 * 1024;    // two CTAs per SM (with the st
 constexpr uint32_t kNodeSmemMax = 4096;          // node tables up to this size are cached per CTA
 
 static_assert(kNL == 8, "the location and group splits below assume eight locations per strip");
-static_assert(kNL <= kWarps && 3 * kNL <= 32, "one warp per location of the strip in phases 1 and 2");
+static_assert(3 * kNL <= 32 && (kNL & (kNL - 1)) == 0, "the strip's records fit one warp's lanes; locations are a power of two");
 static_assert(kUnit == 8, "a unit is a quarter of a 32-bit mask word");
 static_assert(kNL == 8 && kUnit * 4 == 32, "the list builder's lanes are (view of the unit, quarter of the strip)");
 static_assert(kWSlots >= 6, "one lane's slots (two locations, three channels) must fit a run");
@@ -376,21 +376,21 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
             m.need[w0 >> 5] = bal;
     }
 
-    // ---- phases 1 and 2, one warp per location l of the strip: parse the
-    // location's three records, reconstruct its internal nodes level by
-    // level, convert its view parents to RGB
+    // ---- phases 1 and 2, spread over all warps: parse the strip's records
+    // (a warp per record), reconstruct the internal nodes level by level (a
+    // thread per (location, node, channel)), convert the view parents' rows
+    // to RGB (a thread per (location, parent, block row))
     const uint32_t hdr0 = 32 * a.MW;
-    const uint32_t l = warp;   // warps kNL and above only take view units
     // 1a. per record: mask words and the stored blocks in front of each
     // (nothing stored past the end of the row)
-    for (uint32_t c = 0; c < 3 && l < (uint32_t)kNL; c++) {
-        const uint32_t r = 3 * l + c;
+    for (uint32_t r = warp; r < (uint32_t)kRecs; r += kWarps) {
+        const bool live = r < 3 * nl;
         uint32_t *mk = m.mask + r * a.MW;
         uint32_t *mp = m.mpre + r * a.MW;
         const uint32_t *rec = rb + s_roff[r];
         uint32_t P = 0;
         for (uint32_t w0 = 0; w0 < a.MW; w0 += 32) {
-            const uint32_t word = (l < nl && w0 + lane < a.MW) ? rec[w0 + lane] : 0u;
+            const uint32_t word = (live && w0 + lane < a.MW) ? rec[w0 + lane] : 0u;
             const uint32_t cnt = (uint32_t)__popc(word);
             const uint32_t incl = warp_inclusive_scan(cnt, lane);
             if (w0 + lane < a.MW) {
@@ -408,77 +408,77 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
     const uint32_t ob_l = warp_inclusive_scan(np_l, lane) - np_l;
     if (warp == 0 && lane < kRecs)
         s_obase[lane] = ob_l;
-    const uint32_t ob0 = __shfl_sync(kFullMask, ob_l, (3 * l) & 31u);
-    const uint32_t ob1 = __shfl_sync(kFullMask, ob_l, (3 * l + 1) & 31u);
-    const uint32_t ob2 = __shfl_sync(kFullMask, ob_l, (3 * l + 2) & 31u);
-    if (l < nl) {
-        // 1b. per record: payload offset of every stored block (closed-form
-        // lengths of the 18-bit headers, warp scan)
-        for (uint32_t c = 0; c < 3; c++) {
-            const uint32_t r = 3 * l + c;
-            const uint32_t *rec = rb + s_roff[r];
-            const uint32_t P = s_np[r];
-            OffT *o = m_off + (c == 0 ? ob0 : c == 1 ? ob1 : ob2);
-            uint32_t run = hdr0 + kHdrBits * P;
-            for (uint32_t h0 = 0; h0 < P; h0 += 32) {
-                const uint32_t h = h0 + lane;
-                uint32_t len = 0;
-                if (h < P) {
-                    const uint32_t bp = hdr0 + kHdrBits * h;
-                    len = mode_bits(s_mode[__funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 31u]);
-                }
-                const uint32_t incl = warp_inclusive_scan(len, lane);
-                if (h < P)
-                    o[h] = (OffT)(run + incl - len);
-                run += __shfl_sync(kFullMask, incl, 31);
+    // 1b. per record: payload offset of every stored block (closed-form
+    // lengths of the 18-bit headers, warp scan)
+    for (uint32_t r = warp; r < 3 * nl; r += kWarps) {
+        const uint32_t *rec = rb + s_roff[r];
+        const uint32_t P = s_np[r];
+        OffT *o = m_off + __shfl_sync(kFullMask, ob_l, r);
+        uint32_t run = hdr0 + kHdrBits * P;
+        for (uint32_t h0 = 0; h0 < P; h0 += 32) {
+            const uint32_t h = h0 + lane;
+            uint32_t len = 0;
+            if (h < P) {
+                const uint32_t bp = hdr0 + kHdrBits * h;
+                len = mode_bits(s_mode[__funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 31u]);
             }
+            const uint32_t incl = warp_inclusive_scan(len, lane);
+            if (h < P)
+                o[h] = (OffT)(run + incl - len);
+            run += __shfl_sync(kFullMask, incl, 31);
         }
-        __syncwarp();
-        // 2. internal nodes, level by level from the top: reconstruction =
-        // parent reconstruction (top RKV or a node of the level above) +
-        // the decoded residual where a block is stored; one lane per
-        // (node, channel)
-        for (uint32_t lv = 0; lv + 2 < a.L; lv++) {
-            const uint32_t g0 = a.lvl_begin[lv], g1 = a.lvl_begin[lv + 1];
-            const uint32_t *src = lv == 0 ? m.top : m.inter;
-            for (uint32_t q = lane; q < (g1 - g0) * 3; q += 32) {
-                const uint32_t p = g0 + q / 3, c = q - 3 * (q / 3), r = 3 * l + c;
-                const uint32_t word = m.mask[r * a.MW + (p >> 5)];
-                uint32_t v[8];
-                if ((word >> (p & 31u)) & 1u) {
-                    const uint32_t rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
-                    const uint32_t *rec = rb + s_roff[r];
-                    const uint32_t bp = hdr0 + kHdrBits * rank;
-                    const uint32_t hdr = __funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 0x3FFFFu;
-                    const uint32_t pos = m_off[(c == 0 ? ob0 : c == 1 ? ob1 : ob2) + rank];
+    }
+    __syncthreads();
+    // 2. internal nodes, level by level from the top: reconstruction =
+    // parent reconstruction (top RKV or a node of the level above) + the
+    // decoded residual where a block is stored
+    for (uint32_t lv = 0; lv + 2 < a.L; lv++) {
+        const uint32_t g0 = a.lvl_begin[lv], g1 = a.lvl_begin[lv + 1];
+        const uint32_t *src = lv == 0 ? m.top : m.inter;
+        for (uint32_t t = tid; t < (g1 - g0) * 3 * kNL; t += kThreads) {
+            const uint32_t l = t & (kNL - 1), q = t / kNL;
+            if (l >= nl)
+                continue;
+            const uint32_t p = g0 + q / 3, c = q - 3 * (q / 3), r = 3 * l + c;
+            const uint32_t word = m.mask[r * a.MW + (p >> 5)];
+            uint32_t v[8];
+            if ((word >> (p & 31u)) & 1u) {
+                const uint32_t rank = m.mpre[r * a.MW + (p >> 5)] + __popc(word & ((1u << (p & 31u)) - 1u));
+                const uint32_t *rec = rb + s_roff[r];
+                const uint32_t bp = hdr0 + kHdrBits * rank;
+                const uint32_t hdr = __funnelshift_r(rec[bp >> 5], rec[(bp >> 5) + 1], bp) & 0x3FFFFu;
+                const uint32_t pos = m_off[s_obase[r] + rank];
 #ifdef RLFC_DEBUG
-                    if (RLFC_DBG_BLOCK_OK(a.dbg, hdr & 31u, bp + kHdrBits, hdr0 + kHdrBits * s_np[r], pos,
-                                          (hdr & 31u) < (uint32_t)kNumModes ? mode_bits(s_mode[hdr & 31u]) : 0u,
-                                          s_rbits[r]))
-                        decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, v);
-                    else
-                        for (int j = 0; j < 8; j++)
-                            v[j] = kB2;
-#else
+                if (RLFC_DBG_BLOCK_OK(a.dbg, hdr & 31u, bp + kHdrBits, hdr0 + kHdrBits * s_np[r], pos,
+                                      (hdr & 31u) < (uint32_t)kNumModes ? mode_bits(s_mode[hdr & 31u]) : 0u,
+                                      s_rbits[r]))
                     decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, v);
-#endif
-                } else {
-#pragma unroll
+                else
                     for (int j = 0; j < 8; j++)
                         v[j] = kB2;
-                }
-                const uint4 *ps = reinterpret_cast<const uint4 *>(src + (node_parent(nodes[p]) * kNL + l) * 24 + c * 8);
-                uint4 *pd = reinterpret_cast<uint4 *>(m.inter + (p * kNL + l) * 24 + c * 8);
-                const uint4 s0 = ps[0], s1 = ps[1];
-                pd[0] = make_uint4(s0.x + v[0] - kB2, s0.y + v[1] - kB2, s0.z + v[2] - kB2, s0.w + v[3] - kB2);
-                pd[1] = make_uint4(s1.x + v[4] - kB2, s1.y + v[5] - kB2, s1.z + v[6] - kB2, s1.w + v[7] - kB2);
+#else
+                decode_block_pairs(rec, pos, hdr, a.q, s_mode, s_dig, v);
+#endif
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    v[j] = kB2;
             }
-            __syncwarp();
+            const uint4 *ps = reinterpret_cast<const uint4 *>(src + (node_parent(nodes[p]) * kNL + l) * 24 + c * 8);
+            uint4 *pd = reinterpret_cast<uint4 *>(m.inter + (p * kNL + l) * 24 + c * 8);
+            const uint4 s0 = ps[0], s1 = ps[1];
+            pd[0] = make_uint4(s0.x + v[0] - kB2, s0.y + v[1] - kB2, s0.z + v[2] - kB2, s0.w + v[3] - kB2);
+            pd[1] = make_uint4(s1.x + v[4] - kB2, s1.y + v[5] - kB2, s1.z + v[6] - kB2, s1.w + v[7] - kB2);
         }
-        // 3. the location's block rows of every parent of a view, as RGB
+        __syncthreads();
+    }
+    // 3. the block rows of every parent of a view, as RGB
+    {
         const uint32_t *src = a.L == 2 ? m.top : m.inter;
-        for (uint32_t q = lane; q < a.n_par * 4; q += 32) {
-            const uint32_t n = q >> 2, rr = q & 3u;
+        for (uint32_t t = tid; t < a.n_par * 4 * kNL; t += kThreads) {
+            const uint32_t l = t & (kNL - 1), q = t / kNL, n = q >> 2, rr = q & 3u;
+            if (l >= nl)
+                continue;
             const uint32_t *sl = src + ((a.par_base + n) * kNL + l) * 24 + rr * 2;
             uint32_t w[4];
             row_to_rgb<kPacked>(*reinterpret_cast<const uint2 *>(sl), *reinterpret_cast<const uint2 *>(sl + 8),
