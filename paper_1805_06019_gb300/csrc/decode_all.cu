@@ -127,6 +127,7 @@ struct Args {
     uint32_t lvl_begin[kMaxLevels];  // first BFS position of each internal level, top level first; [L-2] = n_int
     uint32_t *dbg;           // debug builds: the stream's flag word
     uint32_t n_out;          // output views (or slots of the packed instantiation)
+    uint32_t ahead;          // CTAs resident at once: the strip this many ahead is prefetched into L2
 };
 
 template <bool kPacked>
@@ -345,6 +346,21 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
     const uint32_t *rb = staged ? m.stage : a.records;   // records base: smem copy or stream
     if (tid < kRecs)
         s_roff[tid] = tid < 3 * (int)nl ? __ldg(a.offsets + 3 * b0 + tid) - (staged ? w_lo : 0u) : 0u;
+    // the records of the strip a CTA of the next wave will take: the last
+    // warp loads their range now and prefetches them into L2 once the parse
+    // is done, so that CTA's staging reads hit L2 instead of DRAM
+    uint32_t pf_lo = 0, pf_hi = 0, pf_top = 0xFFFFFFFFu, pf_nl = 0;   // pf_top, pf_nl: the strip's first location and count
+    {
+        const uint32_t strip2 = blockIdx.y * gridDim.x + blockIdx.x + a.ahead;
+        if (warp == kWarps - 1 && a.ahead && strip2 < gridDim.x * gridDim.y) {
+            const uint32_t bx2 = (strip2 % gridDim.x) * kNL, b02 = (strip2 / gridDim.x) * a.nlx + bx2;
+            const uint32_t nl2 = min((uint32_t)kNL, a.nlx - bx2);
+            pf_lo = __ldg(a.offsets + 3 * b02) & ~31u;
+            pf_hi = __ldg(a.offsets + 3 * (b02 + nl2));
+            pf_top = b02;
+            pf_nl = nl2;
+        }
+    }
 #ifdef RLFC_DEBUG
     if (tid < kRecs)
         s_rbits[tid] = tid < 3 * (int)nl ? 32u * (__ldg(a.offsets + 3 * b0 + tid + 1) - __ldg(a.offsets + 3 * b0 + tid)) : 0u;
@@ -490,6 +506,14 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
         }
     }
     __syncthreads();
+    if (warp == kWarps - 1) {
+        for (uint32_t i = pf_lo + 32u * lane; i < pf_hi; i += 32u * 32u)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.records + i));
+        // the strip's top-RKV blocks: 96 bytes per location, per top RKV
+        if (pf_top != 0xFFFFFFFFu && lane < (int)a.n_top * 6 && (lane % 6) * 64 < pf_nl * 48)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.top + ((size_t)(lane / 6) * a.nloc + pf_top) * 48 +
+                                                          (lane % 6) * 64));
+    }
 
     // ---- phase 3: the views, one unit of kUnit positions at a time per warp.
     // The unit's output rows (kUnit views x 4 rows x the strip's kNL
@@ -719,6 +743,7 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     a.node_smem = t.S <= kNodeSmemMax;
     a.dbg = s->d_debug;
     a.n_out = n_out;
+    a.ahead = 0;
     // internal levels in BFS order: L-2 first, down to 1
     for (uint32_t k = 0; k < (uint32_t)kMaxLevels; k++)
         a.lvl_begin[k] = t.n_int;
@@ -750,6 +775,12 @@ int launch_decode(const rlfc_stream *s, uint8_t *d_out, const uint8_t *needed, c
     if (e != cudaSuccess)
         return cuda_fail(e, "decode_all: shared memory attribute");
     dim3 grid((a.nlx + kNL - 1) / kNL, s->info.nloc_y);
+    {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) == cudaSuccess)
+            a.ahead = (uint32_t)(std::max(sms, 0) * std::max(per_sm, 0));
+    }
     { rlfc::TraceScope trace_((kPacked ? "decode_all_kernel<packed>" : "decode_all_kernel"), st); kern<<<grid, kThreads, smem, st>>>(a); }
     e = cudaGetLastError();
     if (e != cudaSuccess)
