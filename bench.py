@@ -48,9 +48,9 @@ TRAFFIC_PER_LAUNCH = {
     # dram__bytes_read.sum 86.56 MB + dram__bytes_write.sum 3.09 GB)
     ("plain", 4, 1000, "render_native_kernel"): 86_560_000 + 3_090_000_000,
     # decode_all_kernel on the 17x17x1024^2 light field at tau 4 (ncu one-pass, third launch:
-    # dram__bytes_read.sum 98.87 MB + dram__bytes_write.sum 853.17 MB; the rest of the
+    # dram__bytes_read.sum 99.86 MB + dram__bytes_write.sum 852.97 MB; the rest of the
     # 909 MB of output is still in L2 when the kernel ends)
-    ("batching", 4, 0, "decode_all_kernel"): 98_870_000 + 853_170_000,
+    ("batching", 4, 0, "decode_all_kernel"): 99_860_000 + 852_970_000,
 }
 
 # smsp__inst_executed.sum of one launch (warp instructions), from the same kind
@@ -59,7 +59,7 @@ TRAFFIC_PER_LAUNCH = {
 # conversion work bound by instruction issue more than by DRAM
 INSTR_PER_LAUNCH = {
     ("plain", 4, 1000, "render_native_kernel"): 1_072_146_688,
-    ("batching", 4, 0, "decode_all_kernel"): 456_460_687,
+    ("batching", 4, 0, "decode_all_kernel"): 458_440_390,
 }
 # issue peak: 152 SMs x 4 schedulers x one warp instruction per cycle at the
 # 2070 MHz maximum SM clock
