@@ -4,7 +4,7 @@
  *
  * The block header of stream format v1 carries a 2-bit per-block shift s
  * beside the 5-bit BISE mode k (Section 3.3 codes each block with its own
- * range; the shift is this build's extension of that choice).  A kept block's
+ * range; the shift is an extension of that choice, the paper has none).  A kept block's
  * residuals r are then stored as qv = sign(r) floor((|r| + h) / 2^(q+s)),
  * h = 2^(q+s-1) (none when q+s = 0), and reconstructed as qv 2^(q+s): a larger
  * shift shrinks the range to code at the price of distortion.

@@ -2,7 +2,7 @@
 // requests over several CUDA streams, admission by device memory.
 //
 // Threads: callers submit and poll under one mutex; a worker thread admits
-// and launches; CUDA host callbacks (cudaLaunchHostFunc, run by the driver in
+// and launches; CUDA host callbacks (cudaLaunchHostFunc, run by the CUDA driver in
 // stream order after a call's copies to the host) stamp completion, return
 // the call's memory and pinned parameter slot, and wake the worker.  Host
 // callbacks make no CUDA calls.
