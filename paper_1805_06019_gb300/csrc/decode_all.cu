@@ -4,15 +4,17 @@
 // Its 3 * kNL records (location-major, then Y / Co / Cg) are contiguous in the
 // stream; they are copied into shared memory when they fit the CTA's staging
 // budget and read from the stream otherwise.  Phases:
-//  1. parse (one warp per location): the warp stores its three records'
-//     presence masks, the stored-block count in front of each mask word, and
-//     the payload bit offset of every stored block (closed-form lengths of
-//     the 18-bit headers, warp scan);
-//  2. internal nodes (levels >= 1, first in BFS order), by the same warp,
-//     level by level from the top, one lane per (node, channel): the
-//     reconstruction is the parent reconstruction (or top RKV) plus the
-//     decoded residual where a block is stored; then the location's rows of
-//     every parent of a view are converted to RGB once; one barrier, then
+//  1. parse (a warp per record): each record's presence mask, the
+//     stored-block count in front of each mask word, and the payload bit
+//     offset of every stored block (closed-form lengths of the 18-bit
+//     headers, warp scan), in one compact table for the strip;
+//  2. internal nodes (levels >= 1, first in BFS order), level by level from
+//     the top, a thread per (location, node, channel): the reconstruction is
+//     the parent reconstruction (or top RKV) plus the decoded residual where
+//     a block is stored; then a thread per (location, parent, block row)
+//     converts the view parents' rows to RGB.  Barriers separate these steps.
+//     The last warp also prefetches into L2 the records and top-RKV blocks
+//     of the strip a CTA of the next wave will take; then
 //  3. the views, one unit of kUnit (8) BFS positions at a time per warp
 //     (each warp takes the next unit from a shared counter and never waits
 //     for the others).  The unit's output rows (8 views x 4 block rows x
