@@ -522,8 +522,8 @@ RLFC_API int rlfc_mlp_predict(const uint16_t *d_w, const uint16_t *d_x, size_t n
  * Debug builds: the flags the device bounds checks raised for stream s.
  *
  * A library built with RLFC_DEBUG (the build script's debug option) checks,
- * in the full decode, the per-request decode and the binned decode, every
- * stored block before it is decoded: its mode index is one of the 28 BISE
+ * in the full decode, the per-request decode, the binned decode and the
+ * renderer's on-demand decode, every stored block before it is decoded: its mode index is one of the 28 BISE
  * modes, its 18-bit header lies in its record's header area, and its payload
  * lies inside its record (Algorithm 2's record layout, Section 3.4); the
  * full decode also checks every output view index.  A failed check sets a

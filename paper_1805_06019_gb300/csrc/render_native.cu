@@ -512,15 +512,31 @@ __global__ void __launch_bounds__(kThreads, kDecoded ? 4 : 3) render_native_kern
                             word &= (1u << (p & 31u)) - 1u;
                         rp += __popc(word);
                     }
-                    for (uint32_t h = rank; h < rp; h++)
-                        off += mode_bits(s_mode[get_bits(rec, hdr0 + kHdrBits * h, 5)]);
+                    for (uint32_t h = rank; h < rp; h++) {
+                        const uint32_t mh = get_bits(rec, hdr0 + kHdrBits * h, 5);
+#ifdef RLFC_DEBUG
+                        off += mh < (uint32_t)kNumModes ? mode_bits(s_mode[mh]) : 0u;
+#else
+                        off += mode_bits(s_mode[mh]);
+#endif
+                    }
                     rank = rp;
                     cur = p + 1;
                     if ((rec[p >> 5] >> (p & 31u)) & 1u) {
                         const BlockHeader hd = unpack_header(get_bits(rec, hdr0 + kHdrBits * rank, kHdrBits));
-                        my[2 * e] = off | (hd.mode << 22) | (hd.shift << 27) | 0x80000000u;
+#ifdef RLFC_DEBUG
+                        const uint32_t rec_bits = 32u * (a.sv.offsets[3 * loc + c + 1] - a.sv.offsets[3 * loc + c]);
+                        const uint32_t pay = hd.mode < (uint32_t)kNumModes ? mode_bits(s_mode[hd.mode]) : 0u;
+                        const bool ok = RLFC_DBG_BLOCK_OK(a.sv.dbg, hd.mode, hdr0 + kHdrBits * (rank + 1),
+                                                          hdr0 + kHdrBits * P, off, pay, rec_bits);
+#else
+                        constexpr bool ok = true;
+                        const uint32_t pay = mode_bits(s_mode[hd.mode]);
+#endif
+                        // a block that fails the checks of a debug build is left out
+                        my[2 * e] = ok ? (off | (hd.mode << 22) | (hd.shift << 27) | 0x80000000u) : 0u;
                         my[2 * e + 1] = (uint32_t)hd.min;
-                        off += mode_bits(s_mode[hd.mode]);
+                        off += pay;
                         rank++;
                     } else {
                         my[2 * e] = 0u;

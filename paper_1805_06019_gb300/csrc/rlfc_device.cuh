@@ -35,7 +35,8 @@ __device__ __forceinline__ uint32_t mode_b(uint32_t m) { return (m >> 8) & 0xFu;
 __device__ __forceinline__ uint32_t mode_kind(uint32_t m) { return m >> 12; }
 
 // Bounds checks of debug builds (compiled with RLFC_DEBUG).  Before a stored
-// block is decoded, the decoders check it against its record: the mode index
+// block is decoded, the decoders (full, per-request, binned and the
+// renderer's on-demand decode) check it against its record: the mode index
 // is one of the 28, the 18-bit header lies in the record's header area, and
 // the payload lies inside the record.  A failed check sets its bit in the
 // stream's flag word (rlfc_debug_flags) and the block is treated as absent,
