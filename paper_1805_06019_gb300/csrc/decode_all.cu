@@ -510,11 +510,11 @@ __global__ void __launch_bounds__(kThreads, 2) decode_all_kernel(const Args a)
     __syncthreads();
     if (warp == kWarps - 1) {
         for (uint32_t i = pf_lo + 32u * lane; i < pf_hi; i += 32u * 32u)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.records + i));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a.records + i)));
         // the strip's top-RKV blocks: 96 bytes per location, per top RKV
         if (pf_top != 0xFFFFFFFFu && lane < (int)a.n_top * 6 && (lane % 6) * 64 < pf_nl * 48)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.top + ((size_t)(lane / 6) * a.nloc + pf_top) * 48 +
-                                                          (lane % 6) * 64));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(
+                a.top + ((size_t)(lane / 6) * a.nloc + pf_top) * 48 + (lane % 6) * 64)));
     }
 
     // ---- phase 3: the views, one unit of kUnit positions at a time per warp.
