@@ -45,6 +45,17 @@ def test_binding_lists_the_header(lib):
     assert sorted(rlfc.EXPORTS) == _declared()
 
 
+def test_binding_chooses_the_debug_library_only_when_asked(monkeypatch):
+    from paper_1805_06019_gb300 import rlfc
+    monkeypatch.delenv("RLFC_DEBUG_LIBRARY", raising=False)
+    assert rlfc.library_path() == pkg_build.LIB
+    monkeypatch.setenv("RLFC_DEBUG_LIBRARY", "1")
+    assert rlfc.library_path() == pkg_build.LIB_DEBUG
+    monkeypatch.setenv("RLFC_DEBUG_LIBRARY", "0")
+    assert rlfc.library_path() == pkg_build.LIB
+    assert pkg_build.LIB != pkg_build.LIB_DEBUG
+
+
 def test_debug_build_exports_the_same_symbols_and_refuses_null_arguments(lib):
     """The RLFC_DEBUG build (device bounds checks) has the same C ABI; the
     flag query refuses null arguments before any device call, in both builds."""
